@@ -1,0 +1,182 @@
+/*
+ * sgmf.h -- C ABI of the GB300 stereo-LiDAR semi-global matching library.
+ *
+ * The library computes, on one GPU, the pipeline of "Stereo-LiDAR Fusion by
+ * Semi-Global Matching with Discrete Disparity-Matching Cost and
+ * Semidensification" (Yao, Ishikawa, Oishi, RA-L 2025), Fig. 1:
+ *
+ *   sparse LiDAR disparity d-bar  (Sec. IV: integer, aligned with the left view)
+ *   census / Hamming cost H       (Sec. IV-A)
+ *   semidensification d-hat       (Sec. IV-B, Eq. 5)
+ *   joint cost C-bar with DDC     (Sec. IV-A, Eq. 4)
+ *   8-path SGM aggregation        (Sec. III, Eq. 2)
+ *   winner-takes-all d*, d'       (Sec. III, Eq. 3; Sec. IV-C)
+ *   three-view consistency        (Sec. IV-C, Eq. 6)
+ *
+ * Inputs are a rectified stereo pair and a sparse disparity map aligned with
+ * the left (base) image (Sec. II-A, Sec. IV); the output is the consistent
+ * dense disparity map D^{c*} with invalid pixels (Eq. 6).
+ *
+ * Conventions for every entry point:
+ *   - images and maps are row-major, y outermost, pitch = width elements;
+ *   - an invalid disparity is -1 (int16);
+ *   - no C++ exception crosses this ABI; every call returns an sgmf_status
+ *     and, on error, leaves a message for sgmf_last_error();
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef SGMF_H_
+#define SGMF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgmf_ctx sgmf_ctx;
+
+typedef enum {
+    SGMF_OK = 0,
+    SGMF_ERR_ARG = 1,      /* NULL pointer, bad stage id, buffer too small */
+    SGMF_ERR_PARAM = 2,    /* parameter outside the supported range */
+    SGMF_ERR_SHAPE = 3,    /* width/height/disparity range outside the supported range */
+    SGMF_ERR_OOM = 4,      /* device or pinned-host allocation failed */
+    SGMF_ERR_CUDA = 5,     /* a CUDA runtime call or kernel failed */
+    SGMF_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up (kernel returned early) */
+} sgmf_status;
+
+/* Census kinds.  The paper uses the Hamming distance of census-transformed
+ * images after Spangenberg et al. (Sec. IV-A) without giving the window.
+ * Offsets o = (dx, dy), dx in [-4, 4], dy in [-3, 3], are enumerated in
+ * raster order (dy outer, dx inner) without the centre; the k-th offset sets
+ * bit k.  A bit whose compared samples are not all inside the image is 0. */
+enum {
+    SGMF_CENSUS_CS9X7 = 0, /* 31 bits: bit = I(p+o) > I(p-o), the offsets before the centre */
+    SGMF_CENSUS_9X7 = 1    /* 62 bits: bit = I(p+o) > I(p), every offset */
+};
+
+/* Consistency-check variants of Table V. */
+enum {
+    SGMF_CHECK_STEREO_LIDAR = 0, /* Eq. 6: stereo term OR LiDAR term (the method) */
+    SGMF_CHECK_STEREO = 1,       /* stereo term only (left-right check) */
+    SGMF_CHECK_LIDAR = 2,        /* LiDAR term only (camera-LiDAR check) */
+    SGMF_CHECK_NONE = 3          /* no check: D^{c*} = D* */
+};
+
+/* Parameters; sgmf_default_params() fills Table II of the paper. */
+typedef struct {
+    int32_t p1, p2;               /* SGM penalties, Eq. 1/2 (10, 120); 0 <= p1 <= p2 <= 2048 */
+    int32_t q1, q2;               /* DDC penalties, Eq. 4 (5, 160); 0 <= q1 <= q2 */
+    int32_t alpha_num, alpha_den; /* alpha = num/den of Eq. 4 (7/10); 0 <= num <= den, den >= 1 */
+    int32_t ts, rs;               /* semidensification threshold / window radius, Eq. 5 (2, 6); ts <= 65535, rs <= 255 */
+    int32_t tc, rc;               /* consistency threshold / window radius, Eq. 6 (2, 20); tc <= 65535, rc <= 255 */
+    int32_t lr_max_diff;          /* stereo term of Eq. 6: |d* - d'| <= lr_max_diff (1); <= 65535 */
+    int32_t census;               /* SGMF_CENSUS_* (SGMF_CENSUS_CS9X7) */
+    int32_t semidense;            /* 1 = SDSGM, 0 = DSGM (Table I) */
+    int32_t consistency;          /* SGMF_CHECK_* (SGMF_CHECK_STEREO_LIDAR) */
+    int32_t num_paths;            /* 8 (Sec. III) or 4 (horizontal + vertical) */
+} sgmf_params;
+
+/* Intermediate maps that sgmf_debug_stage() can copy out (test use). */
+enum {
+    SGMF_STAGE_DBAR = 0,     /* int16 H x W: sparse map d-bar (Sec. IV) */
+    SGMF_STAGE_CENSUS_L = 1, /* uint64 H x W: census of the left image */
+    SGMF_STAGE_CENSUS_R = 2, /* uint64 H x W: census of the right image */
+    SGMF_STAGE_DHAT = 3,     /* int16 H x W: prior used by the DDC (d-hat, or d-bar for DSGM) */
+    SGMF_STAGE_COST = 4,     /* uint8 H x W x D: joint cost C-bar of Eq. 4 */
+    SGMF_STAGE_SUM = 5,      /* uint16 H x W x D: S = sum_r L_r; only after sgmf_set_debug(c, 1) */
+    SGMF_STAGE_DSTAR = 6,    /* int16 H x W: d* of Eq. 3 */
+    SGMF_STAGE_DPRIME = 7    /* int16 H x W: d' of the right view (diagonal search) */
+};
+
+/* Fill *p with Table II of the paper (and the documented readings). */
+void sgmf_default_params(sgmf_params *p);
+
+/* Create a context for width x height images and max_disp disparities
+ * (d in [0, max_disp - 1]) on the CURRENT CUDA device.  Allocates all device
+ * scratch (census, masks, cost volume, partial sums) once; nothing is
+ * allocated per frame.  Limits: 1 <= width, height <= 8192,
+ * 1 <= max_disp <= 256.  *out receives the context (NULL on error).
+ * Errors: SGMF_ERR_ARG (out NULL), SGMF_ERR_SHAPE, SGMF_ERR_OOM,
+ * SGMF_ERR_CUDA. */
+sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx **out);
+
+/* Validate *p and copy it into the context.  On SGMF_ERR_PARAM the previous
+ * parameters stay in force.  Besides the ranges listed in sgmf_params, the
+ * largest joint cost C-bar (over H <= census bits and q in {0, q1, q2}) must
+ * not exceed 255 (costs are stored as uint8). */
+sgmf_status sgmf_set_params(sgmf_ctx *c, const sgmf_params *p);
+
+/* Copy the context's parameters into *p. */
+sgmf_status sgmf_get_params(const sgmf_ctx *c, sgmf_params *p);
+
+/* Run every later call on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream).  The stream stays owned by the caller. */
+sgmf_status sgmf_set_stream(sgmf_ctx *c, void *cuda_stream);
+
+/* The whole pipeline on DEVICE pointers, enqueued on the context's stream;
+ * returns without waiting.  left, right: uint8 H x W rectified images.
+ * sparse_lidar_disp: float32 H x W LiDAR disparity aligned with the left
+ * image, 0 (or any value <= 0, or non-finite) = no return; NULL = no LiDAR.
+ * out_disp: int16 H x W, receives D^{c*} (-1 invalid).  The caller owns all
+ * four buffers and must keep them alive until the stream reaches this work.
+ * Errors: SGMF_ERR_ARG for NULL images/output; SGMF_ERR_CUDA if a launch
+ * fails; asynchronous device errors surface in sgmf_sync(). */
+sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
+                         const float *sparse_lidar_disp, int16_t *out_disp);
+
+/* The same pipeline on HOST pointers: copies the inputs to device staging
+ * buffers owned by the context, runs sgmf_compute, copies the result back
+ * and waits for the stream.  Pinned host memory gives asynchronous copies;
+ * pageable memory works too.  Same arguments and errors as sgmf_compute,
+ * plus everything sgmf_sync reports. */
+sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
+                              const float *sparse_lidar_disp, int16_t *out_disp);
+
+/* Wait for the context's stream and report the first asynchronous error:
+ * SGMF_ERR_TIMEOUT if a bounded device wait gave up, SGMF_ERR_CUDA for a
+ * CUDA error.  The timeout flag is cleared by this call. */
+sgmf_status sgmf_sync(sgmf_ctx *c);
+
+/* Free the context and everything it allocated.  NULL is allowed. */
+void sgmf_destroy(sgmf_ctx *c);
+
+/* Message of the last failed call on c (never NULL; "" when none).  With
+ * c == NULL, the message of the last failed sgmf_create on this thread. */
+const char *sgmf_last_error(const sgmf_ctx *c);
+
+/* Static name of a status code. */
+const char *sgmf_status_string(sgmf_status s);
+
+/* Keep the aggregate S of the next sgmf_compute calls for
+ * SGMF_STAGE_SUM (allocates H x W x D uint16 once; enable = 0 frees it). */
+sgmf_status sgmf_set_debug(sgmf_ctx *c, int enable);
+
+/* Copy an intermediate of the last sgmf_compute (see SGMF_STAGE_*) into
+ * host memory host_dst of `bytes` bytes; waits for the stream first.
+ * Errors: SGMF_ERR_ARG for an unknown stage, a NULL destination, too few
+ * bytes, or SGMF_STAGE_SUM without sgmf_set_debug(c, 1). */
+sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *host_dst, size_t bytes);
+
+/* Number of kernel launches one sgmf_compute enqueues with the current
+ * parameters (for launch accounting). */
+int sgmf_launches_per_compute(const sgmf_ctx *c);
+
+/* Record CUDA events around every kernel of the following sgmf_compute
+ * calls (enable = 1) or stop (0). */
+sgmf_status sgmf_set_profiling(sgmf_ctx *c, int enable);
+
+/* After sgmf_sync: per-kernel durations (ms) of the last profiled
+ * sgmf_compute.  names[i] (static strings) and ms[i] for i < *n on input
+ * (capacity); *n receives the number of kernels recorded. */
+sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n);
+
+/* Bytes of device memory the context holds. */
+size_t sgmf_device_bytes(const sgmf_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGMF_H_ */

@@ -1,0 +1,465 @@
+// sgmf_api.cu -- the C ABI (include/sgmf.h): contexts, parameter validation,
+// scratch ownership, stream handling and the launch sequence of Fig. 1.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sgmf.h"
+#include "sgmf_internal.cuh"
+
+using namespace sgmf;
+
+struct sgmf_ctx {
+  int device = 0;
+  KParams k{};
+  sgmf_params prm{};
+  cudaStream_t stream = nullptr;
+  Buffers b{};
+  CUtensorMap mapL;   // 64-byte aligned by its declaration
+  CUtensorMap mapR;
+  bool spill8 = true;
+  size_t bytes = 0;
+  std::string err;
+  // device staging for sgmf_compute_host
+  uint8_t *st_left = nullptr, *st_right = nullptr;
+  float *st_lidar = nullptr;
+  int16_t *st_out = nullptr;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char *> names;
+  int nrec = 0;
+  bool computed = false;
+  bool debug = false;
+};
+
+static thread_local std::string g_create_err;
+
+static sgmf_status fail(sgmf_ctx *c, sgmf_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(c, call)                                                                       \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail((c), e_ == cudaErrorMemoryAllocation ? SGMF_ERR_OOM : SGMF_ERR_CUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                               \
+  } while (0)
+
+extern "C" void sgmf_default_params(sgmf_params *p) {
+  if (!p) return;
+  p->p1 = 10;
+  p->p2 = 120;
+  p->q1 = 5;
+  p->q2 = 160;
+  p->alpha_num = 7;
+  p->alpha_den = 10;
+  p->ts = 2;
+  p->rs = 6;
+  p->tc = 2;
+  p->rc = 20;
+  p->lr_max_diff = 1;
+  p->census = SGMF_CENSUS_CS9X7;
+  p->semidense = 1;
+  p->consistency = SGMF_CHECK_STEREO_LIDAR;
+  p->num_paths = 8;
+}
+
+extern "C" const char *sgmf_status_string(sgmf_status s) {
+  switch (s) {
+    case SGMF_OK: return "SGMF_OK";
+    case SGMF_ERR_ARG: return "SGMF_ERR_ARG";
+    case SGMF_ERR_PARAM: return "SGMF_ERR_PARAM";
+    case SGMF_ERR_SHAPE: return "SGMF_ERR_SHAPE";
+    case SGMF_ERR_OOM: return "SGMF_ERR_OOM";
+    case SGMF_ERR_CUDA: return "SGMF_ERR_CUDA";
+    case SGMF_ERR_TIMEOUT: return "SGMF_ERR_TIMEOUT";
+  }
+  return "SGMF_UNKNOWN";
+}
+
+static int census_bits(int kind) { return kind == SGMF_CENSUS_9X7 ? 62 : 31; }
+
+// largest joint cost of Eq. 4 under the integer reading
+static long max_cost(const sgmf_params &p) {
+  const int nb = census_bits(p.census);
+  long mx = nb;   // no prior: C-bar = H
+  const long qs[3] = {0, p.q1, p.q2};
+  for (int h = 0; h <= nb; ++h)
+    for (long q : qs) {
+      const long v = ((long)(p.alpha_den - p.alpha_num) * h + (long)p.alpha_num * q + p.alpha_den / 2) /
+                     p.alpha_den;
+      if (v > mx) mx = v;
+    }
+  return mx;
+}
+
+static sgmf_status validate(const sgmf_params &p, std::string &why) {
+  char buf[256];
+  auto bad = [&](const char *m) {
+    why = m;
+    return SGMF_ERR_PARAM;
+  };
+  if (p.p1 < 0 || p.p2 < p.p1 || p.p2 > 2048) return bad("need 0 <= p1 <= p2 <= 2048");
+  if (p.q1 < 0 || p.q2 < p.q1 || p.q2 > 1000000) return bad("need 0 <= q1 <= q2 (Sec. IV-A)");
+  if (p.alpha_den < 1 || p.alpha_den > 65536 || p.alpha_num < 0 || p.alpha_num > p.alpha_den)
+    return bad("need 0 <= alpha_num <= alpha_den, 1 <= alpha_den <= 65536");
+  if (p.ts < 0 || p.ts > 65535 || p.rs < 0 || p.rs > 255) return bad("need 0 <= ts <= 65535 and 0 <= rs <= 255");
+  if (p.tc < 0 || p.tc > 65535 || p.rc < 0 || p.rc > 255) return bad("need 0 <= tc <= 65535 and 0 <= rc <= 255");
+  if (p.lr_max_diff < 0 || p.lr_max_diff > 65535) return bad("need 0 <= lr_max_diff <= 65535");
+  if (p.census != SGMF_CENSUS_CS9X7 && p.census != SGMF_CENSUS_9X7) return bad("unknown census kind");
+  if (p.semidense != 0 && p.semidense != 1) return bad("semidense must be 0 or 1");
+  if (p.consistency < 0 || p.consistency > 3) return bad("unknown consistency mode");
+  if (p.num_paths != 4 && p.num_paths != 8) return bad("num_paths must be 4 or 8");
+  const long mc = max_cost(p);
+  if (mc > 255) {
+    snprintf(buf, sizeof buf, "largest joint cost %ld exceeds 255 (uint8 cost volume)", mc);
+    why = buf;
+    return SGMF_ERR_PARAM;
+  }
+  return SGMF_OK;
+}
+
+static void apply_params(sgmf_ctx *c, const sgmf_params &p) {
+  c->prm = p;
+  KParams &k = c->k;
+  k.p1 = p.p1;
+  k.p2 = p.p2;
+  k.q1 = p.q1;
+  k.q2 = p.q2;
+  k.a = p.alpha_num;
+  k.b = p.alpha_den;
+  k.ts = p.ts;
+  k.rs = p.rs;
+  k.tc = p.tc;
+  k.rc = p.rc;
+  k.lr = p.lr_max_diff;
+  k.census = p.census;
+  k.semidense = p.semidense;
+  k.consistency = p.consistency;
+  k.num_paths = p.num_paths;
+  k.nbits = census_bits(p.census);
+  c->spill8 = max_cost(p) + p.p2 <= 255;
+}
+
+static void free_all(sgmf_ctx *c) {
+  void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.censL,
+                  c->b.censR, c->b.pres, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
+                  c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.err, c->st_left,
+                  c->st_right, c->st_lidar, c->st_out};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+}
+
+template <typename T>
+static cudaError_t dalloc(sgmf_ctx *c, T **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+  if (e == cudaSuccess) c->bytes += bytes;
+  return e;
+}
+
+extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx **out) {
+  if (!out) return fail(nullptr, SGMF_ERR_ARG, "sgmf_create: out is NULL");
+  *out = nullptr;
+  if (width < 1 || height < 1 || width > kMaxDim || height > kMaxDim || max_disp < 1 || max_disp > kMaxDisp)
+    return fail(nullptr, SGMF_ERR_SHAPE,
+                "sgmf_create: need 1 <= width, height <= %d and 1 <= max_disp <= %d (got %d x %d, D=%d)",
+                kMaxDim, kMaxDisp, width, height, max_disp);
+  sgmf_ctx *c = new (std::nothrow) sgmf_ctx();
+  if (!c) return fail(nullptr, SGMF_ERR_OOM, "sgmf_create: host allocation failed");
+  cudaGetDevice(&c->device);
+  KParams &k = c->k;
+  k.W = width;
+  k.H = height;
+  k.D = max_disp;
+  k.DPL = max_disp <= 64 ? 2 : max_disp <= 128 ? 4 : max_disp <= 192 ? 6 : 8;
+  k.Dp = 32 * k.DPL;
+  k.MW = k.Dp / 32;
+  k.pitch = (width + 15) / 16 * 16;
+  sgmf_params def;
+  sgmf_default_params(&def);
+  apply_params(c, def);
+
+  const size_t n = (size_t)width * height, nv = n * k.Dp;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  A(dalloc(c, &c->b.imgL, (size_t)k.pitch * height));
+  A(dalloc(c, &c->b.imgR, (size_t)k.pitch * height));
+  A(dalloc(c, &c->b.dbar, n * 2));
+  A(dalloc(c, &c->b.dhat, n * 2));
+  A(dalloc(c, &c->b.dstar, n * 2));
+  A(dalloc(c, &c->b.dprime, n * 2));
+  A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censL), n * 8));
+  A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censR), n * 8));
+  A(dalloc(c, &c->b.pres, n * 4 * k.MW));
+  A(dalloc(c, &c->b.boxS, n * 4 * k.MW));
+  A(dalloc(c, &c->b.boxC, n * 4 * k.MW));
+  A(dalloc(c, &c->b.boxTmp, n * 4 * k.MW));
+  A(dalloc(c, &c->b.cost, nv));
+  for (int i = 0; i < 3; ++i) A(dalloc(c, &c->b.part[i], nv * 2));
+  A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), 4 * nv * 2));
+  A(dalloc(c, &c->b.err, sizeof(int)));
+  if (e == cudaSuccess) e = cudaMemset(c->b.err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    sgmf_status s = fail(nullptr, e == cudaErrorMemoryAllocation ? SGMF_ERR_OOM : SGMF_ERR_CUDA,
+                         "sgmf_create: device allocation of %zu bytes failed: %s", c->bytes,
+                         cudaGetErrorString(e));
+    free_all(c);
+    delete c;
+    cudaGetLastError();
+    return s;
+  }
+  if (make_image_tmap(&c->mapL, c->b.imgL, width, height, k.pitch, kCenBoxW, kCenBoxH) != 0 ||
+      make_image_tmap(&c->mapR, c->b.imgR, width, height, k.pitch, kCenBoxW, kCenBoxH) != 0) {
+    free_all(c);
+    delete c;
+    return fail(nullptr, SGMF_ERR_CUDA, "sgmf_create: cuTensorMapEncodeTiled failed");
+  }
+  *out = c;
+  return SGMF_OK;
+}
+
+extern "C" void sgmf_destroy(sgmf_ctx *c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_all(c);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+extern "C" const char *sgmf_last_error(const sgmf_ctx *c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" sgmf_status sgmf_set_params(sgmf_ctx *c, const sgmf_params *p) {
+  if (!c || !p) return fail(c, SGMF_ERR_ARG, "sgmf_set_params: NULL argument");
+  std::string why;
+  if (validate(*p, why) != SGMF_OK) return fail(c, SGMF_ERR_PARAM, "sgmf_set_params: %s", why.c_str());
+  apply_params(c, *p);
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_get_params(const sgmf_ctx *c, sgmf_params *p) {
+  if (!c || !p) return SGMF_ERR_ARG;
+  *p = c->prm;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_set_stream(sgmf_ctx *c, void *stream) {
+  if (!c) return SGMF_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return SGMF_OK;
+}
+
+static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STEREO_LIDAR || k.consistency == SGMF_CHECK_LIDAR; }
+
+extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
+  if (!c) return 0;
+  int n = 5;   // ingest, census, cost, lines, rows
+  if (c->k.semidense) n += 3;
+  if (need_boxc(c->k)) n += 2;
+  n += 1;      // consistency
+  return n;
+}
+
+static void mark(sgmf_ctx *c, const char *name) {
+  if (!c->profiling) return;
+  if (c->nrec >= (int)c->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev.push_back(e);
+    c->names.push_back(nullptr);
+  }
+  c->names[c->nrec] = name;
+  cudaEventRecord(c->ev[c->nrec], c->stream);
+  ++c->nrec;
+}
+
+#define LAUNCH_TRY(c, call)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail((c), SGMF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+extern "C" sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right, const float *lidar,
+                                    int16_t *out) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute: NULL image or output pointer");
+  const KParams &k = c->k;
+  cudaStream_t s = c->stream;
+  c->nrec = 0;
+  mark(c, "ingest");
+  LAUNCH_TRY(c, launch_ingest(k, c->b, left, right, lidar, s));
+  mark(c, "census");
+  LAUNCH_TRY(c, launch_census(k, c->b, &c->mapL, &c->mapR, s));
+  if (k.semidense) {
+    mark(c, "boxor_semidense");
+    LAUNCH_TRY(c, launch_boxor(k, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s, nullptr));
+    mark(c, "semidense");
+    LAUNCH_TRY(c, launch_semidense(k, c->b, s));
+  }
+  mark(c, "cost");
+  LAUNCH_TRY(c, launch_cost(k, c->b, s));
+  mark(c, "agg_lines");
+  LAUNCH_TRY(c, launch_agg_lines(k, c->b, c->spill8, s));
+  mark(c, "agg_rows_wta");
+  LAUNCH_TRY(c, launch_agg_rows(k, c->b, c->spill8, s));
+  if (need_boxc(k)) {
+    mark(c, "boxor_check");
+    LAUNCH_TRY(c, launch_boxor(k, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s, nullptr));
+  }
+  mark(c, "consistency");
+  LAUNCH_TRY(c, launch_consistency(k, c->b, out, s));
+  mark(c, "end");
+  c->computed = true;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_sync(sgmf_ctx *c) {
+  if (!c) return SGMF_ERR_ARG;
+  cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(c, SGMF_ERR_CUDA, "sgmf_sync: %s", cudaGetErrorString(e));
+  int flag = 0;
+  CUDA_TRY(c, cudaMemcpy(&flag, c->b.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag != 0) {
+    CUDA_TRY(c, cudaMemset(c->b.err, 0, sizeof(int)));
+    if (flag == kErrTimeout)
+      return fail(c, SGMF_ERR_TIMEOUT, "sgmf_sync: a bounded device wait gave up (TMA copy did not land)");
+    return fail(c, SGMF_ERR_CUDA, "sgmf_sync: device error word %d", flag);
+  }
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
+                                         const float *lidar, int16_t *out) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute_host: NULL image or output pointer");
+  const size_t n = (size_t)c->k.W * c->k.H;
+  if (!c->st_left) {
+    CUDA_TRY(c, dalloc(c, &c->st_left, n));
+    CUDA_TRY(c, dalloc(c, &c->st_right, n));
+    CUDA_TRY(c, dalloc(c, &c->st_lidar, n * 4));
+    CUDA_TRY(c, dalloc(c, &c->st_out, n * 2));
+  }
+  cudaStream_t s = c->stream;
+  CUDA_TRY(c, cudaMemcpyAsync(c->st_left, left, n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(c->st_right, right, n, cudaMemcpyHostToDevice, s));
+  if (lidar) CUDA_TRY(c, cudaMemcpyAsync(c->st_lidar, lidar, n * 4, cudaMemcpyHostToDevice, s));
+  sgmf_status st = sgmf_compute(c, c->st_left, c->st_right, lidar ? c->st_lidar : nullptr, c->st_out);
+  if (st != SGMF_OK) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->st_out, n * 2, cudaMemcpyDeviceToHost, s));
+  return sgmf_sync(c);
+}
+
+extern "C" sgmf_status sgmf_set_debug(sgmf_ctx *c, int enable) {
+  if (!c) return SGMF_ERR_ARG;
+  if (enable && !c->b.dbg_sum) {
+    CUDA_TRY(c, dalloc(c, &c->b.dbg_sum, (size_t)c->k.W * c->k.H * c->k.Dp * 2));
+  } else if (!enable && c->b.dbg_sum) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->b.dbg_sum);
+    c->bytes -= (size_t)c->k.W * c->k.H * c->k.Dp * 2;
+    c->b.dbg_sum = nullptr;
+  }
+  c->debug = enable != 0;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_t bytes) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!dst) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: NULL destination");
+  const KParams &k = c->k;
+  const size_t n = (size_t)k.W * k.H;
+  size_t need = 0;
+  switch (stage) {
+    case SGMF_STAGE_DBAR: case SGMF_STAGE_DHAT: case SGMF_STAGE_DSTAR: case SGMF_STAGE_DPRIME: need = n * 2; break;
+    case SGMF_STAGE_CENSUS_L: case SGMF_STAGE_CENSUS_R: need = n * 8; break;
+    case SGMF_STAGE_COST: need = n * k.D; break;
+    case SGMF_STAGE_SUM: need = n * k.D * 2; break;
+    default: return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: unknown stage %d", stage);
+  }
+  if (bytes < need) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: need %zu bytes, got %zu", need, bytes);
+  if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum)
+    return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: SUM needs sgmf_set_debug(c, 1) before sgmf_compute");
+  sgmf_status st = sgmf_sync(c);
+  if (st != SGMF_OK) return st;
+  switch (stage) {
+    case SGMF_STAGE_DBAR: CUDA_TRY(c, cudaMemcpy(dst, c->b.dbar, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_DHAT:
+      CUDA_TRY(c, cudaMemcpy(dst, k.semidense ? c->b.dhat : c->b.dbar, need, cudaMemcpyDeviceToHost));
+      break;
+    case SGMF_STAGE_DSTAR: CUDA_TRY(c, cudaMemcpy(dst, c->b.dstar, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_DPRIME: CUDA_TRY(c, cudaMemcpy(dst, c->b.dprime, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_CENSUS_L:
+    case SGMF_STAGE_CENSUS_R: {
+      const void *src = stage == SGMF_STAGE_CENSUS_L ? c->b.censL : c->b.censR;
+      if (k.census == SGMF_CENSUS_9X7) {
+        CUDA_TRY(c, cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+      } else {
+        std::vector<uint32_t> tmp(n);
+        CUDA_TRY(c, cudaMemcpy(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost));
+        uint64_t *o = static_cast<uint64_t *>(dst);
+        for (size_t i = 0; i < n; ++i) o[i] = tmp[i];
+      }
+      break;
+    }
+    case SGMF_STAGE_COST:
+      CUDA_TRY(c, cudaMemcpy2D(dst, k.D, c->b.cost, k.Dp, k.D, n, cudaMemcpyDeviceToHost));
+      break;
+    case SGMF_STAGE_SUM:
+      CUDA_TRY(c, cudaMemcpy2D(dst, (size_t)k.D * 2, c->b.dbg_sum, (size_t)k.Dp * 2, (size_t)k.D * 2, n,
+                               cudaMemcpyDeviceToHost));
+      break;
+  }
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_set_profiling(sgmf_ctx *c, int enable) {
+  if (!c) return SGMF_ERR_ARG;
+  c->profiling = enable != 0;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n) {
+  if (!c || !n) return SGMF_ERR_ARG;
+  const int cap = *n;
+  int cnt = 0;
+  for (int i = 0; i + 1 < c->nrec; ++i) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    if (cnt < cap) {
+      if (names) names[cnt] = c->names[i];
+      if (ms) ms[cnt] = t;
+    }
+    ++cnt;
+  }
+  *n = cnt;
+  return SGMF_OK;
+}
+
+extern "C" size_t sgmf_device_bytes(const sgmf_ctx *c) { return c ? c->bytes : 0; }

@@ -1,0 +1,53 @@
+// sgmf_check.cu -- three-view stereo-LiDAR consistency check, Eq. 6 (Sec. IV-C).
+#include <cstdint>
+
+#include "sgmf_internal.cuh"
+
+namespace sgmf {
+
+// D^{c*}_p = d*_p when
+//   the stereo term holds: q_m = (x - d*, y) is in the image and
+//   |d*_p - d'(q_m)| <= lr, or
+//   the LiDAR term holds: some valid raw d-bar_q, q in the (2rc+1)^2 window
+//   K_p (clipped), has |d*_p - d-bar_q| <= tc -- i.e. the box-ORed presence
+//   mask has a bit in [d* - tc, d* + tc];
+// otherwise -1.  The raw map d-bar is used, never d-hat.  `consistency`
+// selects the Table V variants.
+__global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b, int16_t *__restrict__ out) {
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= k.W || y >= k.H) return;
+  const size_t p = (size_t)y * k.W + x;
+  const int ds = b.dstar[p];
+  bool stereo_ok = false, lidar_ok = false;
+  if (k.consistency != 2 && k.consistency != 3) {
+    const int xm = x - ds;
+    stereo_ok = xm >= 0 && abs(ds - (int)b.dprime[(size_t)y * k.W + xm]) <= k.lr;
+  }
+  if (k.consistency == 0 || k.consistency == 2) {
+    const int lo = max(ds - k.tc, 0), hi = min(ds + k.tc, k.D - 1);
+    const size_t plane = (size_t)k.W * k.H;
+    for (int w = lo >> 5; w <= (hi >> 5) && !lidar_ok; ++w) {
+      const int a = max(lo - 32 * w, 0), e = min(hi - 32 * w, 31);   // bit range [a, e] of word w
+      const uint32_t upto = e == 31 ? 0xffffffffu : ((1u << (e + 1)) - 1u);
+      const uint32_t rng = upto & ~((1u << a) - 1u);
+      lidar_ok = (b.boxC[w * plane + p] & rng) != 0u;
+    }
+  }
+  bool ok;
+  switch (k.consistency) {
+    case 1: ok = stereo_ok; break;
+    case 2: ok = lidar_ok; break;
+    case 3: ok = true; break;
+    default: ok = stereo_ok || lidar_ok; break;
+  }
+  out[p] = ok ? (int16_t)ds : (int16_t)-1;
+}
+
+cudaError_t launch_consistency(const KParams &k, const Buffers &b, int16_t *out, cudaStream_t s) {
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+  k_consistency<<<grid, 256, 0, s>>>(k, b, out);
+  return cudaGetLastError();
+}
+
+}  // namespace sgmf

@@ -1,0 +1,387 @@
+// sgmf_front.cu -- the stages before aggregation (sm_103a):
+//   k_ingest      sparse LiDAR map d-bar + presence masks + pitched image copies
+//   k_census      9x7 census of both images, windows staged in shared memory by TMA
+//   k_boxor_*     separable OR of presence masks over a (2r+1)^2 window
+//   k_semidense   Eq. 5
+//   k_cost        Hamming cost + DDC, Eq. 4, materialised as uint8 [H][W][Dp]
+#include <cuda.h>
+#include <cstdint>
+
+#include "sgmf_internal.cuh"
+
+namespace sgmf {
+
+// --------------------------------------------------------------------------
+// d-bar (Sec. IV: integer sparse disparity aligned with the left view).
+// A LiDAR value f becomes rint(f) (round half to even) when f is finite,
+// f > 0 and rint(f) <= D-1; everything else is invalid (-1).  The presence
+// mask of a pixel has bit d-bar set.  The images are copied into pitched
+// buffers whose rows start on 16-byte boundaries, as TMA requires.
+__global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b, const uint8_t *__restrict__ left,
+                                                const uint8_t *__restrict__ right,
+                                                const float *__restrict__ lidar) {
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= k.W || y >= k.H) return;
+  const size_t p = (size_t)y * k.W + x;
+  int v = -1;
+  if (lidar != nullptr) {
+    const float f = lidar[p];
+    if (isfinite(f) && f > 0.0f) {
+      const float r = rintf(f);
+      if (r <= (float)(k.D - 1)) v = (int)r;
+    }
+  }
+  b.dbar[p] = (int16_t)v;
+  const size_t plane = (size_t)k.W * k.H;
+  for (int w = 0; w < k.MW; ++w)
+    b.pres[w * plane + p] = (v >= 0 && (v >> 5) == w) ? (1u << (v & 31)) : 0u;
+  b.imgL[(size_t)y * k.pitch + x] = left[p];
+  b.imgR[(size_t)y * k.pitch + x] = right[p];
+}
+
+cudaError_t launch_ingest(const KParams &k, const Buffers &b, const uint8_t *left, const uint8_t *right,
+                          const float *lidar, cudaStream_t s) {
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+  k_ingest<<<grid, 256, 0, s>>>(k, b, left, right, lidar);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// TMA helpers (inline PTX).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait: true when the phase completed, false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;   // polls (each try_wait may suspend briefly)
+
+// --------------------------------------------------------------------------
+// Census (Sec. IV-A).  Offsets (dx, dy), dx in [-4,4], dy in [-3,3], in raster
+// order without the centre; offset k sets bit k.  CS 9x7: the 31 offsets
+// before the centre, bit = I(p+o) > I(p-o).  9x7: all 62, bit = I(p+o) > I(p).
+// A bit whose samples are not all inside the image is 0.
+//
+// One CTA computes a 64 x 16 tile of both images.  One thread issues two TMA
+// loads of the 96 x 22 byte boxes starting at (x0-16, y0-3): the x start is a
+// multiple of 16, and samples outside the image arrive as 0 and are masked
+// by the coordinate test on border tiles.
+template <bool FULL>
+__global__ void __launch_bounds__(256) k_census(KParams k, Buffers b, const __grid_constant__ CUtensorMap mapL,
+                                                const __grid_constant__ CUtensorMap mapR) {
+  // each box starts on a 128-byte boundary, as cp.async.bulk.tensor requires
+  constexpr int kBoxBytes = (kCenBoxH * kCenBoxW + 127) / 128 * 128;
+  __shared__ alignas(128) uint8_t tiles[2 * kBoxBytes];
+  __shared__ alignas(8) uint64_t bar;
+  const int x0 = blockIdx.x * kCenTileW, y0 = blockIdx.y * kCenTileH;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, 2u * kCenBoxW * kCenBoxH);
+    tma_load_2d(tiles, &mapL, x0 - 16, y0 - 3, &bar);
+    tma_load_2d(tiles + kBoxBytes, &mapR, x0 - 16, y0 - 3, &bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0, kWaitLimit)) {
+    set_error(b.err, kErrTimeout);
+    mbar_wait_bounded(&bar, 0, kWaitLimit);   // give the copies in flight a second chance
+    return;
+  }
+  const bool interior = x0 >= 4 && x0 + kCenTileW + 4 <= k.W && y0 >= 3 && y0 + kCenTileH + 3 <= k.H;
+  const int tx = threadIdx.x & 63;
+  const int x = x0 + tx;
+  for (int r = threadIdx.x >> 6; r < kCenTileH; r += 4) {
+    const int y = y0 + r;
+    if (x >= k.W || y >= k.H) continue;
+    const int sx = tx + 16, sy = r + 3;
+#pragma unroll
+    for (int img = 0; img < 2; ++img) {
+      const uint8_t(*T)[kCenBoxW] = reinterpret_cast<const uint8_t(*)[kCenBoxW]>(tiles + img * kBoxBytes);
+      uint64_t c = 0;
+      int bit = 0;
+#pragma unroll
+      for (int dy = -3; dy <= 3; ++dy) {
+#pragma unroll
+        for (int dx = -4; dx <= 4; ++dx) {
+          if (dx == 0 && dy == 0) {
+            if (!FULL) goto done;
+            continue;
+          }
+          {
+            const uint8_t a = T[sy + dy][sx + dx];
+            bool v;
+            bool inside = true;
+            if (FULL) {
+              v = a > T[sy][sx];
+              if (!interior) inside = (unsigned)(x + dx) < (unsigned)k.W && (unsigned)(y + dy) < (unsigned)k.H;
+            } else {
+              v = a > T[sy - dy][sx - dx];
+              if (!interior)
+                inside = (unsigned)(x + dx) < (unsigned)k.W && (unsigned)(y + dy) < (unsigned)k.H &&
+                         (unsigned)(x - dx) < (unsigned)k.W && (unsigned)(y - dy) < (unsigned)k.H;
+            }
+            if (v && inside) c |= (uint64_t)1 << bit;
+            ++bit;
+          }
+        }
+      }
+    done:
+      const size_t p = (size_t)y * k.W + x;
+      if (FULL)
+        static_cast<uint64_t *>(img ? b.censR : b.censL)[p] = c;
+      else
+        static_cast<uint32_t *>(img ? b.censR : b.censL)[p] = (uint32_t)c;
+    }
+  }
+}
+
+cudaError_t launch_census(const KParams &k, const Buffers &b, const void *tmaL, const void *tmaR,
+                          cudaStream_t s) {
+  dim3 grid((k.W + kCenTileW - 1) / kCenTileW, (k.H + kCenTileH - 1) / kCenTileH);
+  const CUtensorMap &mL = *static_cast<const CUtensorMap *>(tmaL);
+  const CUtensorMap &mR = *static_cast<const CUtensorMap *>(tmaR);
+  if (k.census == 1)
+    k_census<true><<<grid, 256, 0, s>>>(k, b, mL, mR);
+  else
+    k_census<false><<<grid, 256, 0, s>>>(k, b, mL, mR);
+  return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch, int box_w, int box_h) {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || ptr == nullptr)
+      return -1;
+    fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(static_cast<CUtensorMap *>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<uint8_t *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+// --------------------------------------------------------------------------
+// Separable box-OR of presence masks: dst[w][y][x] = OR of src[w][y'][x'] over
+// |x'-x| <= r, |y'-y| <= r inside the image.  The OR over a clipped rectangle
+// is the OR (over rows) of the ORs along each row, so a row pass followed by
+// a column pass is exact.
+constexpr int kBoxRowTile = 256;
+
+__global__ void __launch_bounds__(kBoxRowTile) k_boxor_rows(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                           int W, int H, int r) {
+  extern __shared__ uint32_t seg[];
+  const int y = blockIdx.y, w = blockIdx.z;
+  const size_t base = ((size_t)w * H + y) * W;
+  const int x0 = blockIdx.x * kBoxRowTile;
+  const int n = kBoxRowTile + 2 * r;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int x = x0 - r + i;
+    seg[i] = (x >= 0 && x < W) ? src[base + x] : 0u;
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x;
+  if (x >= W) return;
+  uint32_t acc = 0;
+  for (int i = 0; i <= 2 * r; ++i) acc |= seg[threadIdx.x + i];
+  dst[base + x] = acc;
+}
+
+constexpr int kBoxColW = 32, kBoxColH = 64;
+
+__global__ void __launch_bounds__(256) k_boxor_cols(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                   int W, int H, int r) {
+  extern __shared__ uint32_t blk[];   // [(kBoxColH + 2r)][kBoxColW]
+  const int w = blockIdx.z;
+  const size_t plane = (size_t)w * H * W;
+  const int x0 = blockIdx.x * kBoxColW, y0 = blockIdx.y * kBoxColH;
+  const int rows = kBoxColH + 2 * r;
+  const int tx = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < rows; i += 8) {
+    const int y = y0 - r + i, x = x0 + tx;
+    blk[i * kBoxColW + tx] = (y >= 0 && y < H && x < W) ? src[plane + (size_t)y * W + x] : 0u;
+  }
+  __syncthreads();
+  const int x = x0 + tx;
+  if (x >= W) return;
+  for (int oy = threadIdx.x >> 5; oy < kBoxColH; oy += 8) {
+    const int y = y0 + oy;
+    if (y >= H) break;
+    uint32_t acc = 0;
+    for (int i = 0; i <= 2 * r; ++i) acc |= blk[(oy + i) * kBoxColW + tx];
+    dst[plane + (size_t)y * W + x] = acc;
+  }
+}
+
+cudaError_t launch_boxor(const KParams &k, const uint32_t *src, uint32_t *tmp, uint32_t *dst, int radius,
+                         cudaStream_t s, int *nlaunch) {
+  dim3 g1((k.W + kBoxRowTile - 1) / kBoxRowTile, k.H, k.MW);
+  size_t sm1 = (size_t)(kBoxRowTile + 2 * radius) * sizeof(uint32_t);
+  k_boxor_rows<<<g1, kBoxRowTile, sm1, s>>>(src, tmp, k.W, k.H, radius);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 g2((k.W + kBoxColW - 1) / kBoxColW, (k.H + kBoxColH - 1) / kBoxColH, k.MW);
+  size_t sm2 = (size_t)(kBoxColH + 2 * radius) * kBoxColW * sizeof(uint32_t);
+  k_boxor_cols<<<g2, 256, sm2, s>>>(tmp, dst, k.W, k.H, radius);
+  if (nlaunch) *nlaunch += 2;
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Semidensification, Eq. 5 (Sec. IV-B).  The candidates of pixel p are the
+// distinct valid d-bar_q, q in the (2rs+1)^2 window: exactly the set bits of
+// the box-ORed presence mask.  Visiting them in increasing d and keeping the
+// first strict minimum of H(p, d) gives the smallest H with ties to the
+// smaller disparity.  d-hat = that d if min H < ts, else d-bar_p.
+template <typename CT>
+__global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b) {
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= k.W || y >= k.H) return;
+  const size_t p = (size_t)y * k.W + x;
+  const size_t plane = (size_t)k.W * k.H;
+  const CT *cl = static_cast<const CT *>(b.censL);
+  const CT *cr = static_cast<const CT *>(b.censR);
+  const CT c = cl[p];
+  int best_h = 0x7fffffff, best_d = -1;
+  for (int w = 0; w < k.MW && best_h > 0; ++w) {
+    uint32_t m = b.boxS[w * plane + p];
+    while (m != 0u) {
+      const int d = w * 32 + __ffs(m) - 1;
+      m &= m - 1u;
+      const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr[p - d])) : k.nbits;
+      if (h < best_h) {
+        best_h = h;
+        best_d = d;
+        if (h == 0) break;
+      }
+    }
+  }
+  b.dhat[p] = (best_d >= 0 && best_h < k.ts) ? (int16_t)best_d : b.dbar[p];
+}
+
+cudaError_t launch_semidense(const KParams &k, const Buffers &b, cudaStream_t s) {
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+  if (k.census == 1)
+    k_semidense<uint64_t><<<grid, 256, 0, s>>>(k, b);
+  else
+    k_semidense<uint32_t><<<grid, 256, 0, s>>>(k, b);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Joint cost C-bar (Eq. 4).  H(p,d) = popcount(cL(x,y) ^ cR(x-d,y)), or the
+// number of census bits where x - d < 0.  Where the prior (d-hat, or d-bar
+// for DSGM) is invalid C-bar = H; otherwise
+//   C-bar = floor(((b-a) H + a q + floor(b/2)) / b),  q = 0 / q1 / q2 for
+// |d - prior| = 0 / 1 / > 1, looked up in a table built on the host.
+// Each thread writes 4 consecutive disparities of one pixel (one u32);
+// cells d >= D hold 0.
+struct CostTable {
+  uint8_t v[3][64];   // [q class][H]
+};
+
+template <typename CT>
+__global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b, const __grid_constant__ CostTable tab) {
+  const int groups = k.Dp >> 2;   // threads per pixel
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t npx = (size_t)k.W * k.H;
+  const size_t p = gid / groups;
+  if (p >= npx) return;
+  const int g = (int)(gid - p * groups);
+  const int x = (int)(p % k.W);
+  const CT *cl = static_cast<const CT *>(b.censL);
+  const CT *cr = static_cast<const CT *>(b.censR);
+  const int16_t *prior = k.semidense ? b.dhat : b.dbar;
+  const CT c = cl[p];
+  const int pd = prior[p];
+  uint32_t out = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int d = g * 4 + j;
+    uint32_t v = 0;
+    if (d < k.D) {
+      const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr[p - d])) : k.nbits;
+      if (pd < 0) {
+        v = (uint32_t)h;
+      } else {
+        const int ad = abs(d - pd);
+        const int cls = ad == 0 ? 0 : (ad == 1 ? 1 : 2);
+        v = tab.v[cls][h];
+      }
+    }
+    out |= v << (8 * j);
+  }
+  reinterpret_cast<uint32_t *>(b.cost)[gid] = out;
+}
+
+cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s) {
+  CostTable tab;
+  const int qs[3] = {0, k.q1, k.q2};
+  for (int c = 0; c < 3; ++c)
+    for (int h = 0; h < 64; ++h) {
+      const long v = ((long)(k.b - k.a) * h + (long)k.a * qs[c] + k.b / 2) / k.b;
+      tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
+    }
+  const size_t threads = (size_t)k.W * k.H * (k.Dp / 4);
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  if (k.census == 1)
+    k_cost<uint64_t><<<blocks, 256, 0, s>>>(k, b, tab);
+  else
+    k_cost<uint32_t><<<blocks, 256, 0, s>>>(k, b, tab);
+  return cudaGetLastError();
+}
+
+}  // namespace sgmf

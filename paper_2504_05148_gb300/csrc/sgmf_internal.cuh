@@ -1,0 +1,87 @@
+// sgmf_internal.cuh -- shared declarations of the CUDA library (sm_103a).
+//
+// Device data layout (all row-major, y outermost):
+//   images          uint8  [H][pitch]      pitched copies (pitch % 16 == 0) for TMA
+//   d-bar, d-hat    int16  [H][W]          -1 = invalid
+//   census          u32 (CS 9x7) or u64 (9x7) [H][W]
+//   presence masks  u32    [MW][H][W]      bit d of word-plane d/32 set when the
+//                                           pixel's (or window's) sparse disparity is d
+//   cost C-bar      uint8  [H][W][Dp]      Dp = 32 * DPL >= D, cells d >= D hold 0
+//   partial sums    u16    [H][W][Dp]      one per line family (vertical, two diagonals)
+//   spills          uint8/u16 [line][pos][Dp]  first-direction path costs of a line
+//
+// A warp owns one SGM line; lane l holds disparities [l*DPL, (l+1)*DPL) as
+// DPL/2 words of two u16 halves (low half = even disparity).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sgmf {
+
+constexpr int kMaxDisp = 256;
+constexpr int kMaxDim = 8192;
+constexpr uint32_t kInf = 0x4000u;          // u16 lane value above every real path cost
+constexpr uint32_t kInf2 = kInf | (kInf << 16);
+
+enum ErrorCode : int { kErrNone = 0, kErrTimeout = 6 };
+
+// Parameters in the form the kernels use (validated on the host).
+struct KParams {
+  int W, H, D, Dp, DPL, MW;   // MW = Dp / 32 mask words per pixel
+  int pitch;                  // image pitch in bytes
+  int p1, p2, q1, q2, a, b;   // alpha = a / b
+  int ts, rs, tc, rc, lr;
+  int census, semidense, consistency, num_paths;
+  int nbits;                  // census bits (31 or 62)
+};
+
+struct Buffers {
+  uint8_t *imgL, *imgR;       // pitched copies
+  int16_t *dbar, *dhat, *dstar, *dprime;
+  void *censL, *censR;        // u32 or u64 per pixel
+  uint32_t *pres, *boxS, *boxC, *boxTmp;   // [MW][H][W]
+  uint8_t *cost;              // [H][W][Dp]
+  uint16_t *part[3];          // [H][W][Dp]
+  void *spill;                // 4 regions (vertical, diag, anti-diag, rows) of H*W*Dp elements
+  uint16_t *dbg_sum;          // [H][W][Dp] or null
+  int *err;                   // device error word
+};
+
+// ---- small device helpers ------------------------------------------------
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
+  return __byte_perm(a, b, s);
+}
+
+// sticky error word: first error wins
+__device__ __forceinline__ void set_error(int *err, int code) {
+  atomicCAS(err, 0, code);
+}
+
+// ---- kernel launchers (implemented in the .cu files) -----------------------
+struct TmaMaps;   // opaque holder of the two image tensor maps (sgmf_front.cu)
+
+cudaError_t launch_ingest(const KParams &k, const Buffers &b, const uint8_t *left,
+                          const uint8_t *right, const float *lidar, cudaStream_t s);
+cudaError_t launch_census(const KParams &k, const Buffers &b, const void *tmaL, const void *tmaR,
+                          cudaStream_t s);
+cudaError_t launch_boxor(const KParams &k, const uint32_t *src, uint32_t *tmp, uint32_t *dst,
+                         int radius, cudaStream_t s, int *nlaunch);
+cudaError_t launch_semidense(const KParams &k, const Buffers &b, cudaStream_t s);
+cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s);
+cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, bool spill8, cudaStream_t s);
+cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, bool spill8, cudaStream_t s);
+cudaError_t launch_consistency(const KParams &k, const Buffers &b, int16_t *out, cudaStream_t s);
+
+// host: encode the 2-D uint8 tensor map of a pitched image (driver entry point)
+int make_image_tmap(void *tmap_out /* CUtensorMap* */, const uint8_t *base, int W, int H, int pitch,
+                    int box_w, int box_h);
+
+// census tile geometry (shared by host map creation and the kernel)
+constexpr int kCenTileW = 64;     // output pixels per tile, x
+constexpr int kCenTileH = 16;     // output pixels per tile, y
+constexpr int kCenBoxW = 96;      // loaded box: x0-16 .. x0+79 (16-byte aligned start)
+constexpr int kCenBoxH = 22;      // loaded box: y0-3 .. y0+18
+
+}  // namespace sgmf

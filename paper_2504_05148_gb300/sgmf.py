@@ -1,0 +1,303 @@
+"""ctypes binding of the C ABI in ``include/sgmf.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments: all stages of the pipeline run in the CUDA
+kernels of ``libsgmf.so``.  There is no CPU fallback; if the library is
+missing or cannot be loaded, ``lib()`` raises.
+
+``Context`` is a small convenience wrapper that passes torch tensors (device
+memory, streams) to the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, asdict, fields
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsgmf.so")
+
+SGMF_OK, SGMF_ERR_ARG, SGMF_ERR_PARAM, SGMF_ERR_SHAPE, SGMF_ERR_OOM, SGMF_ERR_CUDA, SGMF_ERR_TIMEOUT = range(7)
+SGMF_CENSUS_CS9X7, SGMF_CENSUS_9X7 = 0, 1
+SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 0, 1, 2, 3
+(SGMF_STAGE_DBAR, SGMF_STAGE_CENSUS_L, SGMF_STAGE_CENSUS_R, SGMF_STAGE_DHAT, SGMF_STAGE_COST,
+ SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME) = range(8)
+
+# symbols declared in include/sgmf.h
+EXPORTS = (
+    "sgmf_default_params", "sgmf_create", "sgmf_set_params", "sgmf_get_params", "sgmf_set_stream",
+    "sgmf_compute", "sgmf_compute_host", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
+    "sgmf_status_string", "sgmf_set_debug", "sgmf_debug_stage", "sgmf_launches_per_compute",
+    "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes",
+)
+
+
+class SgmfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class sgmf_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in (
+        "p1", "p2", "q1", "q2", "alpha_num", "alpha_den", "ts", "rs", "tc", "rc",
+        "lr_max_diff", "census", "semidense", "consistency", "num_paths")]
+
+
+@dataclass
+class Params:
+    """Mirror of sgmf_params; defaults are Table II of the paper."""
+
+    p1: int = 10
+    p2: int = 120
+    q1: int = 5
+    q2: int = 160
+    alpha_num: int = 7
+    alpha_den: int = 10
+    ts: int = 2
+    rs: int = 6
+    tc: int = 2
+    rc: int = 20
+    lr_max_diff: int = 1
+    census: int = SGMF_CENSUS_CS9X7
+    semidense: int = 1
+    consistency: int = SGMF_CHECK_STEREO_LIDAR
+    num_paths: int = 8
+
+    def to_c(self) -> sgmf_params:
+        return sgmf_params(**asdict(self))
+
+    @classmethod
+    def from_c(cls, c: sgmf_params) -> "Params":
+        return cls(**{f.name: getattr(c, f.name) for f in fields(cls)})
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libsgmf.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} not built: run __graft_entry__.build() or "
+                                "python paper_2504_05148_gb300/build.py")
+    L = ctypes.CDLL(path)
+    P, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    ctx_pp = ctypes.POINTER(ctypes.c_void_p)
+    prm_p = ctypes.POINTER(sgmf_params)
+    sig = {
+        "sgmf_default_params": (None, [prm_p]),
+        "sgmf_create": (i, [i, i, i, ctx_pp]),
+        "sgmf_set_params": (i, [P, prm_p]),
+        "sgmf_get_params": (i, [P, prm_p]),
+        "sgmf_set_stream": (i, [P, P]),
+        "sgmf_compute": (i, [P, P, P, P, P]),
+        "sgmf_compute_host": (i, [P, P, P, P, P]),
+        "sgmf_sync": (i, [P]),
+        "sgmf_destroy": (None, [P]),
+        "sgmf_last_error": (ctypes.c_char_p, [P]),
+        "sgmf_status_string": (ctypes.c_char_p, [i]),
+        "sgmf_set_debug": (i, [P, i]),
+        "sgmf_debug_stage": (i, [P, i, P, sz]),
+        "sgmf_launches_per_compute": (i, [P]),
+        "sgmf_set_profiling": (i, [P, i]),
+        "sgmf_kernel_times": (i, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_int)]),
+        "sgmf_device_bytes": (sz, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().sgmf_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _check(status: int, ctx=None) -> None:
+    if status != SGMF_OK:
+        raise SgmfError(status, lib().sgmf_last_error(ctx).decode())
+
+
+# ---- one function per entry point ---------------------------------------------
+
+def sgmf_default_params() -> Params:
+    c = sgmf_params()
+    lib().sgmf_default_params(ctypes.byref(c))
+    return Params.from_c(c)
+
+
+def sgmf_create(width: int, height: int, max_disp: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().sgmf_create(width, height, max_disp, ctypes.byref(out)), None)
+    return out.value
+
+
+def sgmf_set_params(ctx: int, params: Params) -> None:
+    c = params.to_c()
+    _check(lib().sgmf_set_params(ctx, ctypes.byref(c)), ctx)
+
+
+def sgmf_get_params(ctx: int) -> Params:
+    c = sgmf_params()
+    _check(lib().sgmf_get_params(ctx, ctypes.byref(c)), ctx)
+    return Params.from_c(c)
+
+
+def sgmf_set_stream(ctx: int, stream: int | None) -> None:
+    _check(lib().sgmf_set_stream(ctx, stream or None), ctx)
+
+
+def sgmf_compute(ctx: int, left: int, right: int, lidar: int | None, out: int) -> None:
+    """Device pointers (ints); lidar may be None."""
+    _check(lib().sgmf_compute(ctx, left, right, lidar or None, out), ctx)
+
+
+def sgmf_compute_host(ctx: int, left: int, right: int, lidar: int | None, out: int) -> None:
+    """Host pointers (ints); lidar may be None.  Waits for the result."""
+    _check(lib().sgmf_compute_host(ctx, left, right, lidar or None, out), ctx)
+
+
+def sgmf_sync(ctx: int) -> None:
+    _check(lib().sgmf_sync(ctx), ctx)
+
+
+def sgmf_destroy(ctx: int | None) -> None:
+    lib().sgmf_destroy(ctx)
+
+
+def sgmf_last_error(ctx: int | None) -> str:
+    return lib().sgmf_last_error(ctx).decode()
+
+
+def sgmf_set_debug(ctx: int, enable: bool) -> None:
+    _check(lib().sgmf_set_debug(ctx, int(bool(enable))), ctx)
+
+
+def sgmf_debug_stage(ctx: int, stage: int, host_ptr: int, nbytes: int) -> None:
+    _check(lib().sgmf_debug_stage(ctx, stage, host_ptr, nbytes), ctx)
+
+
+def sgmf_launches_per_compute(ctx: int) -> int:
+    return lib().sgmf_launches_per_compute(ctx)
+
+
+def sgmf_set_profiling(ctx: int, enable: bool) -> None:
+    _check(lib().sgmf_set_profiling(ctx, int(bool(enable))), ctx)
+
+
+def sgmf_kernel_times(ctx: int, cap: int = 32) -> list[tuple[str, float]]:
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    n = ctypes.c_int(cap)
+    _check(lib().sgmf_kernel_times(ctx, names, ms, ctypes.byref(n)), ctx)
+    return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+
+def sgmf_device_bytes(ctx: int) -> int:
+    return lib().sgmf_device_bytes(ctx)
+
+
+# ---- torch convenience wrapper ------------------------------------------------------
+
+class Context:
+    """Owns one sgmf context for a (width, height, max_disp) shape."""
+
+    def __init__(self, width: int, height: int, max_disp: int, params: Params | None = None,
+                 stream=None):
+        self.W, self.H, self.D = width, height, max_disp
+        self.handle = sgmf_create(width, height, max_disp)
+        if params is not None:
+            sgmf_set_params(self.handle, params)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream) -> None:
+        sgmf_set_stream(self.handle, getattr(stream, "cuda_stream", stream))
+
+    def set_params(self, params: Params) -> None:
+        sgmf_set_params(self.handle, params)
+
+    def compute(self, left, right, lidar, out) -> None:
+        """torch CUDA tensors: uint8 (H, W) x2, float32 (H, W) or None, int16 (H, W)."""
+        for t, dt in ((left, "torch.uint8"), (right, "torch.uint8"), (out, "torch.int16")):
+            if str(t.dtype) != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (self.H, self.W):
+                raise ValueError(f"expected contiguous CUDA {dt} of shape {(self.H, self.W)}")
+        lp = None
+        if lidar is not None:
+            if str(lidar.dtype) != "torch.float32" or not lidar.is_cuda or not lidar.is_contiguous() \
+                    or tuple(lidar.shape) != (self.H, self.W):
+                raise ValueError("lidar must be a contiguous CUDA float32 (H, W) tensor or None")
+            lp = lidar.data_ptr()
+        sgmf_compute(self.handle, left.data_ptr(), right.data_ptr(), lp, out.data_ptr())
+
+    def compute_host(self, left, right, lidar, out) -> None:
+        """numpy (or CPU torch) arrays; blocks until `out` holds the result."""
+        import numpy as np
+        for a, dt in ((left, np.uint8), (right, np.uint8), (out, np.int16)):
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"] or a.shape != (self.H, self.W):
+                raise ValueError(f"expected C-contiguous {dt} of shape {(self.H, self.W)}")
+        lp = None
+        if lidar is not None:
+            if lidar.dtype != np.float32 or not lidar.flags["C_CONTIGUOUS"] or lidar.shape != (self.H, self.W):
+                raise ValueError("lidar must be C-contiguous float32 (H, W) or None")
+            lp = lidar.ctypes.data
+        sgmf_compute_host(self.handle, left.ctypes.data, right.ctypes.data, lp, out.ctypes.data)
+
+    def sync(self) -> None:
+        sgmf_sync(self.handle)
+
+    def stage(self, stage: int):
+        """Copy an intermediate of the last compute to a numpy array."""
+        import numpy as np
+        shape2 = (self.H, self.W)
+        spec = {
+            SGMF_STAGE_DBAR: (np.int16, shape2), SGMF_STAGE_DHAT: (np.int16, shape2),
+            SGMF_STAGE_DSTAR: (np.int16, shape2), SGMF_STAGE_DPRIME: (np.int16, shape2),
+            SGMF_STAGE_CENSUS_L: (np.uint64, shape2), SGMF_STAGE_CENSUS_R: (np.uint64, shape2),
+            SGMF_STAGE_COST: (np.uint8, shape2 + (self.D,)), SGMF_STAGE_SUM: (np.uint16, shape2 + (self.D,)),
+        }[stage]
+        a = np.empty(spec[1], spec[0])
+        sgmf_debug_stage(self.handle, stage, a.ctypes.data, a.nbytes)
+        return a
+
+    def set_debug(self, enable: bool) -> None:
+        sgmf_set_debug(self.handle, enable)
+
+    def launches_per_compute(self) -> int:
+        return sgmf_launches_per_compute(self.handle)
+
+    def set_profiling(self, enable: bool) -> None:
+        sgmf_set_profiling(self.handle, enable)
+
+    def kernel_times(self):
+        return sgmf_kernel_times(self.handle)
+
+    def device_bytes(self) -> int:
+        return sgmf_device_bytes(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            sgmf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
