@@ -48,36 +48,6 @@ cudaError_t launch_ingest(const KParams &k, const Buffers &b, const uint8_t *lef
 }
 
 // --------------------------------------------------------------------------
-// TMA helpers (inline PTX).
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
@@ -85,15 +55,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-
-// bounded wait: true when the phase completed, false after `limit` polls
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-constexpr uint32_t kWaitLimit = 1u << 22;   // polls (each try_wait may suspend briefly)
 
 // --------------------------------------------------------------------------
 // Census (Sec. IV-A).  Offsets (dx, dy), dx in [-4,4], dy in [-3,3], in raster
@@ -327,44 +288,75 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, cudaStream_t s)
 // for DSGM) is invalid C-bar = H; otherwise
 //   C-bar = floor(((b-a) H + a q + floor(b/2)) / b),  q = 0 / q1 / q2 for
 // |d - prior| = 0 / 1 / > 1, looked up in a table built on the host.
-// Each thread writes 4 consecutive disparities of one pixel (one u32);
-// cells d >= D hold 0.
+// A CTA handles 32 pixels of one row: their right-census window is staged in
+// shared memory, and consecutive threads write consecutive 4-cell words of
+// the [x][Dp] cost rows (cells d >= D hold 0).
 struct CostTable {
   uint8_t v[3][64];   // [q class][H]
 };
 
-template <typename CT>
+constexpr int kCostPx = 32;
+
+template <typename CT, int DPL>
 __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b, const __grid_constant__ CostTable tab) {
-  const int groups = k.Dp >> 2;   // threads per pixel
-  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t npx = (size_t)k.W * k.H;
-  const size_t p = gid / groups;
-  if (p >= npx) return;
-  const int g = (int)(gid - p * groups);
-  const int x = (int)(p % k.W);
-  const CT *cl = static_cast<const CT *>(b.censL);
-  const CT *cr = static_cast<const CT *>(b.censR);
-  const int16_t *prior = k.semidense ? b.dhat : b.dbar;
-  const CT c = cl[p];
-  const int pd = prior[p];
-  uint32_t out = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int d = g * 4 + j;
-    uint32_t v = 0;
-    if (d < k.D) {
-      const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr[p - d])) : k.nbits;
-      if (pd < 0) {
-        v = (uint32_t)h;
-      } else {
-        const int ad = abs(d - pd);
-        const int cls = ad == 0 ? 0 : (ad == 1 ? 1 : 2);
-        v = tab.v[cls][h];
-      }
-    }
-    out |= v << (8 * j);
+  constexpr int Dp = 32 * DPL, G = Dp / 4;      // 4-cell words per pixel
+  __shared__ CT cr_s[kCostPx + Dp];
+  __shared__ CT cl_s[kCostPx];
+  __shared__ int pd_s[kCostPx];
+  __shared__ uint8_t tab_s[3 * 64];
+  const int x0 = blockIdx.x * kCostPx, y = blockIdx.y, W = k.W;
+  const size_t rowp = (size_t)y * W;
+  const CT *cl = static_cast<const CT *>(b.censL) + rowp;
+  const CT *cr = static_cast<const CT *>(b.censR) + rowp;
+  const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
+  const int base = x0 - (Dp - 1);               // cr_s[i] = cR(base + i)
+  for (int i = threadIdx.x; i < kCostPx + Dp - 1; i += blockDim.x) {
+    const int xx = base + i;
+    cr_s[i] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
   }
-  reinterpret_cast<uint32_t *>(b.cost)[gid] = out;
+  if (threadIdx.x < kCostPx) {
+    const int xx = x0 + threadIdx.x;
+    cl_s[threadIdx.x] = xx < W ? cl[xx] : (CT)0;
+    pd_s[threadIdx.x] = xx < W ? prior[xx] : -1;
+  }
+  for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
+  __syncthreads();
+  uint32_t *out = reinterpret_cast<uint32_t *>(b.cost + rowp * Dp);
+  for (int j = threadIdx.x; j < kCostPx * G; j += blockDim.x) {
+    const int px = j / G, g = j - px * G;
+    const int x = x0 + px;
+    if (x >= W) break;                          // j grows with px: the rest is past the row
+    const CT c = cl_s[px];
+    const int pd = pd_s[px];
+    uint32_t word = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int d = 4 * g + i;
+      uint32_t v = 0;
+      if (d < k.D) {
+        const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr_s[x - d - base])) : k.nbits;
+        if (pd < 0) {
+          v = (uint32_t)h;
+        } else {
+          const int ad = abs(d - pd);
+          v = tab_s[(ad == 0 ? 0 : (ad == 1 ? 64 : 128)) + h];
+        }
+      }
+      word |= v << (8 * i);
+    }
+    out[(size_t)x * G + g] = word;
+  }
+}
+
+template <typename CT>
+static void launch_cost_t(const KParams &k, const Buffers &b, const CostTable &tab, cudaStream_t s) {
+  dim3 grid((k.W + kCostPx - 1) / kCostPx, k.H);
+  switch (k.DPL) {
+    case 2: k_cost<CT, 2><<<grid, 256, 0, s>>>(k, b, tab); break;
+    case 4: k_cost<CT, 4><<<grid, 256, 0, s>>>(k, b, tab); break;
+    case 6: k_cost<CT, 6><<<grid, 256, 0, s>>>(k, b, tab); break;
+    default: k_cost<CT, 8><<<grid, 256, 0, s>>>(k, b, tab); break;
+  }
 }
 
 cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s) {
@@ -375,12 +367,10 @@ cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s) {
       const long v = ((long)(k.b - k.a) * h + (long)k.a * qs[c] + k.b / 2) / k.b;
       tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
     }
-  const size_t threads = (size_t)k.W * k.H * (k.Dp / 4);
-  const unsigned blocks = (unsigned)((threads + 255) / 256);
   if (k.census == 1)
-    k_cost<uint64_t><<<blocks, 256, 0, s>>>(k, b, tab);
+    launch_cost_t<uint64_t>(k, b, tab, s);
   else
-    k_cost<uint32_t><<<blocks, 256, 0, s>>>(k, b, tab);
+    launch_cost_t<uint32_t>(k, b, tab, s);
   return cudaGetLastError();
 }
 
