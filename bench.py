@@ -5,8 +5,8 @@
 Workload: 1242 x 375 stereo pairs with D = 128 and 64-beam LiDAR (about 5 %
 density), the KITTI-shaped synthetic scene of paper_2504_05148_gb300.scenes;
 the full method (SDSGM: semidensification, DDC, 8 paths, WTA, three-view
-check).  One step = the whole pipeline over a batch of B frames; the frames
-of a step run concurrently, one context and one CUDA stream each.  Inputs
+check).  One step = the whole pipeline over a batch of B frames, one call of
+sgmf_compute_batch: every kernel launch covers all B frames.  Inputs
 are resident in HBM before the timed region; L2 is flushed (512 MiB write)
 between steps, outside the timed events.  Under torchrun every rank runs
 its own frames (weak scaling, no collective on the data path); the step time
@@ -33,7 +33,7 @@ UNIT = "W*H*D/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
-# Algorithmic work per launch of each kernel, per frame (V = W*H*D cells, N = W*H pixels).
+# Algorithmic work of each kernel for V = W*H*D cells and N = W*H pixels.
 # bytes: data the stage must read and write in HBM given its inputs and outputs
 #        (spills and re-reads chosen by the implementation are not counted);
 # ops:   scalar integer operations of the method (Eq. 2: 2 adds of P1, 3 mins,
@@ -88,7 +88,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -181,9 +181,9 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -203,40 +203,30 @@ def main():
     dev = torch.device("cuda", local)
     B = args.batch
     frames = make_frames(B, rank)
-    streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
-    ctxs = [sgmf.Context(W, H, D, stream=st) for st in streams]
-    dl = [torch.from_numpy(f.left).to(dev) for f in frames]
-    dr = [torch.from_numpy(f.right).to(dev) for f in frames]
-    dli = [torch.from_numpy(f.lidar).to(dev) for f in frames]
-    dout = [torch.empty((H, W), dtype=torch.int16, device=dev) for _ in frames]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = sgmf.Context(W, H, D, stream=stream, max_batch=B)
+    dl = torch.from_numpy(np.stack([f.left for f in frames])).to(dev)
+    dr = torch.from_numpy(np.stack([f.right for f in frames])).to(dev)
+    dli = torch.from_numpy(np.stack([f.lidar for f in frames])).to(dev)
+    dout = torch.empty((B, H, W), dtype=torch.int16, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    main_s = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
 
-    def step(profile: bool):
+    def step():
         start = torch.cuda.Event(enable_timing=True)
         stop = torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        start.record(main_s)
-        ends = []
-        for i in range(B):
-            streams[i].wait_event(start)
-            ctxs[i].compute(dl[i], dr[i], dli[i], dout[i])
-            e = torch.cuda.Event()
-            e.record(streams[i])
-            ends.append(e)
-        for e in ends:
-            main_s.wait_event(e)
-        stop.record(main_s)
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush, outside the timed events
+            start.record(stream)
+            ctx.compute(dl, dr, dli, dout)
+            stop.record(stream)
         return start, stop
 
-    for c in ctxs:
-        c.set_profiling(True)
+    ctx.set_profiling(True)
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize(dev)
-    for c in ctxs:
-        c.sync()
+    ctx.sync()
     if pg:
         import torch.distributed as dist
         dist.barrier()
@@ -246,19 +236,16 @@ def main():
     total_ms = 0.0
     ktimes: dict[str, list[float]] = {}
     for _ in range(args.steps):
-        a, b = step(True)
+        a, b = step()
         b.synchronize()
         total_ms += a.elapsed_time(b)
-        for c in ctxs:
-            for name, ms in c.kernel_times():
-                ktimes.setdefault(name, []).append(ms)
+        for name, ms in ctx.kernel_times():
+            ktimes.setdefault(name, []).append(ms)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    for c in ctxs:
-        c.sync()
-    launches = args.steps * B * ctxs[0].launches_per_compute()
+    ctx.sync()
+    launches = args.steps * ctx.launches_per_compute()
 
-    # correctness spot check of the timed outputs against the first warm-up-free call
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if pg:
         import torch.distributed as dist
@@ -271,40 +258,31 @@ def main():
     # end to end through the public host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
-        from concurrent.futures import ThreadPoolExecutor
-        hl = [torch.from_numpy(f.left).pin_memory().numpy() for f in frames]
-        hr = [torch.from_numpy(f.right).pin_memory().numpy() for f in frames]
-        hli = [torch.from_numpy(f.lidar).pin_memory().numpy() for f in frames]
-        ho = [torch.empty((H, W), dtype=torch.int16).pin_memory().numpy() for _ in frames]
-        for c in ctxs:
-            c.set_profiling(False)
-        pool = ThreadPoolExecutor(max_workers=B)
-
-        def host_step():
-            list(pool.map(lambda i: ctxs[i].compute_host(hl[i], hr[i], hli[i], ho[i]), range(B)))
-
+        hl = torch.from_numpy(np.stack([f.left for f in frames])).pin_memory().numpy()
+        hr = torch.from_numpy(np.stack([f.right for f in frames])).pin_memory().numpy()
+        hli = torch.from_numpy(np.stack([f.lidar for f in frames])).pin_memory().numpy()
+        ho = torch.empty((B, H, W), dtype=torch.int16).pin_memory().numpy()
+        ctx.set_profiling(False)
         for _ in range(args.warmup):
-            host_step()
+            ctx.compute_host(hl, hr, hli, ho)
         if pg:
             import torch.distributed as dist
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            host_step()
+            ctx.compute_host(hl, hr, hli, ho)
         dt = time.perf_counter() - t0
         te = torch.tensor([dt], dtype=torch.float64, device=dev)
         if pg:
             import torch.distributed as dist
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         dt = float(te.item())
-        pool.shutdown()
         e2e = {"value": frames_total * W * H * D / dt, "unit": UNIT,
                "h2d_bytes_per_step": B * (W * H * 2 + W * H * 4), "d2h_bytes_per_step": B * W * H * 2,
                "frames_per_s": frames_total / dt}
         # the host results must equal the device results
-        for i in range(B):
-            if not np.array_equal(ho[i], dout[i].cpu().numpy()):
-                raise RuntimeError("host entry point result differs from the device result")
+        if not np.array_equal(ho, dout.cpu().numpy()):
+            raise RuntimeError("host entry point result differs from the device result")
 
     if rank != 0:
         if pg:
@@ -317,7 +295,7 @@ def main():
     avg = {k: sum(v) / len(v) for k, v in ktimes.items()}
     tot = {k: sum(v) for k, v in ktimes.items()}
     dom = max(tot, key=tot.get)
-    V, N = W * H * D, W * H
+    V, N = W * H * D * B, W * H * B          # every launch covers the B frames of a step
     alg = algorithmic(dom, V, N)
     sm_mhz = (clk or {}).get("sm_mhz") or peaks["sm_max_mhz"]
     alu_peak = 152 * 64 * 2 * sm_mhz * 1e6       # u16x2 lanes of the ALU pipe, per second
@@ -358,7 +336,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
         "frames_per_s": frames_total / (total_ms * 1e-3),
         "config": {"workload": WORKLOAD, "W": W, "H": H, "D": D, "frames_per_step": B,
-                   "streams_per_gpu": B, "l2": "flushed by a 512 MiB write between steps",
+                   "batched_launch": True, "l2": "flushed by a 512 MiB write between steps",
                    "lidar": "64 beams, ~5% density", "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
@@ -366,8 +344,7 @@ def main():
         "paper_context": {"sdsgm_ms_per_frame": 50, "hardware": "Jetson Orin NX 16GB", "data": "KITTI 141"},
     }
     print(json.dumps(line), flush=True)
-    for c in ctxs:
-        c.close()
+    ctx.close()
     if pg:
         import torch.distributed as dist
         dist.destroy_process_group()

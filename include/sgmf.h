@@ -102,6 +102,15 @@ void sgmf_default_params(sgmf_params *p);
  * SGMF_ERR_CUDA. */
 sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx **out);
 
+/* As sgmf_create, for batches: the context holds device buffers for up to
+ * max_batch frames (1 <= max_batch <= 4096) of the same shape, which
+ * sgmf_compute_batch processes in one pass of every kernel (each launch
+ * covers all frames).  Device memory grows linearly with max_batch. */
+sgmf_status sgmf_create_batched(int width, int height, int max_disp, int max_batch, sgmf_ctx **out);
+
+/* Number of frames the context's buffers hold (its max_batch). */
+int sgmf_batch_capacity(const sgmf_ctx *c);
+
 /* Validate *p and copy it into the context.  On SGMF_ERR_PARAM the previous
  * parameters stay in force.  Besides the ranges listed in sgmf_params, the
  * largest joint cost C-bar (over H <= census bits and q in {0, q1, q2}) must
@@ -126,6 +135,14 @@ sgmf_status sgmf_set_stream(sgmf_ctx *c, void *cuda_stream);
 sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
                          const float *sparse_lidar_disp, int16_t *out_disp);
 
+/* The pipeline on n frames at once (1 <= n <= the batch capacity), DEVICE
+ * pointers: left, right, out hold n contiguous H x W frames ([n][H][W]);
+ * sparse_lidar_disp is [n][H][W] float32 or NULL (no LiDAR for any frame).
+ * Same ownership, stream and error behaviour as sgmf_compute; the frames are
+ * independent (sgmf_compute is this call with n = 1). */
+sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                               const float *sparse_lidar_disp, int16_t *out_disp);
+
 /* The same pipeline on HOST pointers: copies the inputs to device staging
  * buffers owned by the context, runs sgmf_compute, copies the result back
  * and waits for the stream.  Pinned host memory gives asynchronous copies;
@@ -133,6 +150,11 @@ sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
  * plus everything sgmf_sync reports. */
 sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
                               const float *sparse_lidar_disp, int16_t *out_disp);
+
+/* sgmf_compute_host for n frames ([n][H][W] host buffers), with the
+ * copies of all n frames in and out around one sgmf_compute_batch. */
+sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                    const float *sparse_lidar_disp, int16_t *out_disp);
 
 /* Wait for the context's stream and report the first asynchronous error:
  * SGMF_ERR_TIMEOUT if a bounded device wait gave up, SGMF_ERR_CUDA for a
@@ -149,12 +171,13 @@ const char *sgmf_last_error(const sgmf_ctx *c);
 /* Static name of a status code. */
 const char *sgmf_status_string(sgmf_status s);
 
-/* Keep the aggregate S of the next sgmf_compute calls for
+/* Keep the aggregate S of frame 0 of the next sgmf_compute calls for
  * SGMF_STAGE_SUM (allocates H x W x D uint16 once; enable = 0 frees it). */
 sgmf_status sgmf_set_debug(sgmf_ctx *c, int enable);
 
-/* Copy an intermediate of the last sgmf_compute (see SGMF_STAGE_*) into
- * host memory host_dst of `bytes` bytes; waits for the stream first.
+/* Copy an intermediate of frame 0 of the last sgmf_compute or
+ * sgmf_compute_batch (see SGMF_STAGE_*) into host memory host_dst of `bytes`
+ * bytes; waits for the stream first.
  * Errors: SGMF_ERR_ARG for an unknown stage, a NULL destination, too few
  * bytes, or SGMF_STAGE_SUM without sgmf_set_debug(c, 1). */
 sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *host_dst, size_t bytes);

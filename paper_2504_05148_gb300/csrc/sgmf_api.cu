@@ -17,6 +17,7 @@ using namespace sgmf;
 
 struct sgmf_ctx {
   int device = 0;
+  int nb = 1;                  // frames the buffers hold (batch capacity)
   KParams k{};
   sgmf_params prm{};
   cudaStream_t stream = nullptr;
@@ -36,6 +37,7 @@ struct sgmf_ctx {
   std::vector<const char *> names;
   int nrec = 0;
   bool computed = false;
+  int last_n = 0;
   bool debug = false;
 };
 
@@ -177,15 +179,22 @@ static cudaError_t dalloc(sgmf_ctx *c, T **p, size_t bytes) {
 }
 
 extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx **out) {
+  return sgmf_create_batched(width, height, max_disp, 1, out);
+}
+
+extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, int max_batch, sgmf_ctx **out) {
   if (!out) return fail(nullptr, SGMF_ERR_ARG, "sgmf_create: out is NULL");
   *out = nullptr;
   if (width < 1 || height < 1 || width > kMaxDim || height > kMaxDim || max_disp < 1 || max_disp > kMaxDisp)
     return fail(nullptr, SGMF_ERR_SHAPE,
                 "sgmf_create: need 1 <= width, height <= %d and 1 <= max_disp <= %d (got %d x %d, D=%d)",
                 kMaxDim, kMaxDisp, width, height, max_disp);
+  if (max_batch < 1 || max_batch > 4096)
+    return fail(nullptr, SGMF_ERR_SHAPE, "sgmf_create_batched: need 1 <= max_batch <= 4096 (got %d)", max_batch);
   sgmf_ctx *c = new (std::nothrow) sgmf_ctx();
   if (!c) return fail(nullptr, SGMF_ERR_OOM, "sgmf_create: host allocation failed");
   cudaGetDevice(&c->device);
+  c->nb = max_batch;
   KParams &k = c->k;
   k.W = width;
   k.H = height;
@@ -198,13 +207,13 @@ extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx
   sgmf_default_params(&def);
   apply_params(c, def);
 
-  const size_t n = (size_t)width * height, nv = n * k.Dp;
+  const size_t n = (size_t)width * height * max_batch, nv = n * k.Dp;   // all frames
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  A(dalloc(c, &c->b.imgL, (size_t)k.pitch * height));
-  A(dalloc(c, &c->b.imgR, (size_t)k.pitch * height));
+  A(dalloc(c, &c->b.imgL, (size_t)k.pitch * height * max_batch));
+  A(dalloc(c, &c->b.imgR, (size_t)k.pitch * height * max_batch));
   A(dalloc(c, &c->b.dbar, n * 2));
   A(dalloc(c, &c->b.dhat, n * 2));
   A(dalloc(c, &c->b.dstar, n * 2));
@@ -229,8 +238,8 @@ extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx
     cudaGetLastError();
     return s;
   }
-  if (make_image_tmap(&c->mapL, c->b.imgL, width, height, k.pitch, kCenBoxW, kCenBoxH) != 0 ||
-      make_image_tmap(&c->mapR, c->b.imgR, width, height, k.pitch, kCenBoxW, kCenBoxH) != 0) {
+  if (make_image_tmap(&c->mapL, c->b.imgL, width, height, k.pitch, max_batch, kCenBoxW, kCenBoxH) != 0 ||
+      make_image_tmap(&c->mapR, c->b.imgR, width, height, k.pitch, max_batch, kCenBoxW, kCenBoxH) != 0) {
     free_all(c);
     delete c;
     return fail(nullptr, SGMF_ERR_CUDA, "sgmf_create: cuTensorMapEncodeTiled failed");
@@ -279,7 +288,7 @@ static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STE
 
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (!c) return 0;
-  int n = 5;   // ingest, census, cost, lines, rows
+  int n = 4 + (c->k.num_paths == 8 ? 3 : 1);   // ingest, census, cost, rows + one line launch per family
   if (c->k.semidense) n += 3;
   if (need_boxc(c->k)) n += 2;
   n += 1;      // consistency
@@ -306,38 +315,46 @@ static void mark(sgmf_ctx *c, const char *name) {
       return fail((c), SGMF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
-extern "C" sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right, const float *lidar,
-                                    int16_t *out) {
+extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                          const float *lidar, int16_t *out) {
   if (!c) return SGMF_ERR_ARG;
   if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute: NULL image or output pointer");
+  if (n < 1 || n > c->nb)
+    return fail(c, SGMF_ERR_ARG, "sgmf_compute_batch: need 1 <= n <= %d frames (got %d)", c->nb, n);
   const KParams &k = c->k;
   cudaStream_t s = c->stream;
   c->nrec = 0;
   mark(c, "ingest");
-  LAUNCH_TRY(c, launch_ingest(k, c->b, left, right, lidar, s));
+  LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
   mark(c, "census");
-  LAUNCH_TRY(c, launch_census(k, c->b, &c->mapL, &c->mapR, s));
+  LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
   if (k.semidense) {
     mark(c, "boxor_semidense");
-    LAUNCH_TRY(c, launch_boxor(k, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s, nullptr));
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s));
     mark(c, "semidense");
-    LAUNCH_TRY(c, launch_semidense(k, c->b, s));
+    LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
   }
   mark(c, "cost");
-  LAUNCH_TRY(c, launch_cost(k, c->b, s));
+  LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
   mark(c, "agg_lines");
-  LAUNCH_TRY(c, launch_agg_lines(k, c->b, c->spill8, s));
+  LAUNCH_TRY(c, launch_agg_lines(k, c->b, n, c->spill8, s));
   mark(c, "agg_rows_wta");
-  LAUNCH_TRY(c, launch_agg_rows(k, c->b, c->spill8, s));
+  LAUNCH_TRY(c, launch_agg_rows(k, c->b, n, c->spill8, s));
   if (need_boxc(k)) {
     mark(c, "boxor_check");
-    LAUNCH_TRY(c, launch_boxor(k, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s, nullptr));
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s));
   }
   mark(c, "consistency");
-  LAUNCH_TRY(c, launch_consistency(k, c->b, out, s));
+  LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
   mark(c, "end");
   c->computed = true;
+  c->last_n = n;
   return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_compute(sgmf_ctx *c, const uint8_t *left, const uint8_t *right, const float *lidar,
+                                    int16_t *out) {
+  return sgmf_compute_batch(c, 1, left, right, lidar, out);
 }
 
 extern "C" sgmf_status sgmf_sync(sgmf_ctx *c) {
@@ -355,26 +372,36 @@ extern "C" sgmf_status sgmf_sync(sgmf_ctx *c) {
   return SGMF_OK;
 }
 
-extern "C" sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
-                                         const float *lidar, int16_t *out) {
+extern "C" sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int nf, const uint8_t *left, const uint8_t *right,
+                                               const float *lidar, int16_t *out) {
   if (!c) return SGMF_ERR_ARG;
   if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute_host: NULL image or output pointer");
-  const size_t n = (size_t)c->k.W * c->k.H;
+  if (nf < 1 || nf > c->nb)
+    return fail(c, SGMF_ERR_ARG, "sgmf_compute_host_batch: need 1 <= n <= %d frames (got %d)", c->nb, nf);
+  const size_t cap = (size_t)c->k.W * c->k.H * c->nb;
+  const size_t n = (size_t)c->k.W * c->k.H * nf;
   if (!c->st_left) {
-    CUDA_TRY(c, dalloc(c, &c->st_left, n));
-    CUDA_TRY(c, dalloc(c, &c->st_right, n));
-    CUDA_TRY(c, dalloc(c, &c->st_lidar, n * 4));
-    CUDA_TRY(c, dalloc(c, &c->st_out, n * 2));
+    CUDA_TRY(c, dalloc(c, &c->st_left, cap));
+    CUDA_TRY(c, dalloc(c, &c->st_right, cap));
+    CUDA_TRY(c, dalloc(c, &c->st_lidar, cap * 4));
+    CUDA_TRY(c, dalloc(c, &c->st_out, cap * 2));
   }
   cudaStream_t s = c->stream;
   CUDA_TRY(c, cudaMemcpyAsync(c->st_left, left, n, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(c->st_right, right, n, cudaMemcpyHostToDevice, s));
   if (lidar) CUDA_TRY(c, cudaMemcpyAsync(c->st_lidar, lidar, n * 4, cudaMemcpyHostToDevice, s));
-  sgmf_status st = sgmf_compute(c, c->st_left, c->st_right, lidar ? c->st_lidar : nullptr, c->st_out);
+  sgmf_status st = sgmf_compute_batch(c, nf, c->st_left, c->st_right, lidar ? c->st_lidar : nullptr, c->st_out);
   if (st != SGMF_OK) return st;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->st_out, n * 2, cudaMemcpyDeviceToHost, s));
   return sgmf_sync(c);
 }
+
+extern "C" sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,
+                                         const float *lidar, int16_t *out) {
+  return sgmf_compute_host_batch(c, 1, left, right, lidar, out);
+}
+
+extern "C" int sgmf_batch_capacity(const sgmf_ctx *c) { return c ? c->nb : 0; }
 
 extern "C" sgmf_status sgmf_set_debug(sgmf_ctx *c, int enable) {
   if (!c) return SGMF_ERR_ARG;

@@ -13,10 +13,12 @@ namespace sgmf {
 //   mask has a bit in [d* - tc, d* + tc];
 // otherwise -1.  The raw map d-bar is used, never d-hat.  `consistency`
 // selects the Table V variants.
-__global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b, int16_t *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b0, int16_t *__restrict__ out) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= k.W || y >= k.H) return;
+  const Buffers b = frame_view(k, b0, blockIdx.z);
+  out += (size_t)blockIdx.z * frame_px(k);
   const size_t p = (size_t)y * k.W + x;
   const int ds = b.dstar[p];
   bool stereo_ok = false, lidar_ok = false;
@@ -44,8 +46,8 @@ __global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b, int16
   out[p] = ok ? (int16_t)ds : (int16_t)-1;
 }
 
-cudaError_t launch_consistency(const KParams &k, const Buffers &b, int16_t *out, cudaStream_t s) {
-  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s) {
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8, nf);
   k_consistency<<<grid, 256, 0, s>>>(k, b, out);
   return cudaGetLastError();
 }

@@ -17,12 +17,18 @@ namespace sgmf {
 // f > 0 and rint(f) <= D-1; everything else is invalid (-1).  The presence
 // mask of a pixel has bit d-bar set.  The images are copied into pitched
 // buffers whose rows start on 16-byte boundaries, as TMA requires.
-__global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b, const uint8_t *__restrict__ left,
+__global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b0, const uint8_t *__restrict__ left,
                                                 const uint8_t *__restrict__ right,
                                                 const float *__restrict__ lidar) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= k.W || y >= k.H) return;
+  const int f = blockIdx.z;
+  const Buffers b = frame_view(k, b0, f);
+  const size_t fo = (size_t)f * frame_px(k);
+  left += fo;
+  right += fo;
+  if (lidar != nullptr) lidar += fo;
   const size_t p = (size_t)y * k.W + x;
   int v = -1;
   if (lidar != nullptr) {
@@ -40,19 +46,19 @@ __global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b, const uint
   b.imgR[(size_t)y * k.pitch + x] = right[p];
 }
 
-cudaError_t launch_ingest(const KParams &k, const Buffers &b, const uint8_t *left, const uint8_t *right,
+cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint8_t *left, const uint8_t *right,
                           const float *lidar, cudaStream_t s) {
-  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8, nf);
   k_ingest<<<grid, 256, 0, s>>>(k, b, left, right, lidar);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
           "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -67,8 +73,10 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 // multiple of 16, and samples outside the image arrive as 0 and are masked
 // by the coordinate test on border tiles.
 template <bool FULL>
-__global__ void __launch_bounds__(256) k_census(KParams k, Buffers b, const __grid_constant__ CUtensorMap mapL,
+__global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __grid_constant__ CUtensorMap mapL,
                                                 const __grid_constant__ CUtensorMap mapR) {
+  const int f = blockIdx.z;
+  const Buffers b = frame_view(k, b0, f);
   // each box starts on a 128-byte boundary, as cp.async.bulk.tensor requires
   constexpr int kBoxBytes = (kCenBoxH * kCenBoxW + 127) / 128 * 128;
   __shared__ alignas(128) uint8_t tiles[2 * kBoxBytes];
@@ -81,8 +89,8 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b, const __gr
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, 2u * kCenBoxW * kCenBoxH);
-    tma_load_2d(tiles, &mapL, x0 - 16, y0 - 3, &bar);
-    tma_load_2d(tiles + kBoxBytes, &mapR, x0 - 16, y0 - 3, &bar);
+    tma_load_3d(tiles, &mapL, x0 - 16, y0 - 3, f, &bar);
+    tma_load_3d(tiles + kBoxBytes, &mapR, x0 - 16, y0 - 3, f, &bar);
   }
   if (!mbar_wait_bounded(&bar, 0, kWaitLimit)) {
     set_error(b.err, kErrTimeout);
@@ -137,9 +145,9 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b, const __gr
   }
 }
 
-cudaError_t launch_census(const KParams &k, const Buffers &b, const void *tmaL, const void *tmaR,
+cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
                           cudaStream_t s) {
-  dim3 grid((k.W + kCenTileW - 1) / kCenTileW, (k.H + kCenTileH - 1) / kCenTileH);
+  dim3 grid((k.W + kCenTileW - 1) / kCenTileW, (k.H + kCenTileH - 1) / kCenTileH, nf);
   const CUtensorMap &mL = *static_cast<const CUtensorMap *>(tmaL);
   const CUtensorMap &mR = *static_cast<const CUtensorMap *>(tmaR);
   if (k.census == 1)
@@ -154,7 +162,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                   CUtensorMapFloatOOBfill);
 
-int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch, int box_w, int box_h) {
+int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch, int frames, int box_w,
+                    int box_h) {
   static EncodeTiledFn fn = nullptr;
   if (fn == nullptr) {
     void *ptr = nullptr;
@@ -164,11 +173,11 @@ int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch
       return -1;
     fn = reinterpret_cast<EncodeTiledFn>(ptr);
   }
-  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(static_cast<CUtensorMap *>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)frames};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * H};
+  cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(static_cast<CUtensorMap *>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                   const_cast<uint8_t *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -2;
@@ -226,17 +235,17 @@ __global__ void __launch_bounds__(256) k_boxor_cols(const uint32_t *__restrict__
   }
 }
 
-cudaError_t launch_boxor(const KParams &k, const uint32_t *src, uint32_t *tmp, uint32_t *dst, int radius,
-                         cudaStream_t s, int *nlaunch) {
-  dim3 g1((k.W + kBoxRowTile - 1) / kBoxRowTile, k.H, k.MW);
+cudaError_t launch_boxor(const KParams &k, int nf, const uint32_t *src, uint32_t *tmp, uint32_t *dst, int radius,
+                         cudaStream_t s) {
+  // frames and mask words are contiguous planes: plane z = f * MW + w
+  dim3 g1((k.W + kBoxRowTile - 1) / kBoxRowTile, k.H, nf * k.MW);
   size_t sm1 = (size_t)(kBoxRowTile + 2 * radius) * sizeof(uint32_t);
   k_boxor_rows<<<g1, kBoxRowTile, sm1, s>>>(src, tmp, k.W, k.H, radius);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 g2((k.W + kBoxColW - 1) / kBoxColW, (k.H + kBoxColH - 1) / kBoxColH, k.MW);
+  dim3 g2((k.W + kBoxColW - 1) / kBoxColW, (k.H + kBoxColH - 1) / kBoxColH, nf * k.MW);
   size_t sm2 = (size_t)(kBoxColH + 2 * radius) * kBoxColW * sizeof(uint32_t);
   k_boxor_cols<<<g2, 256, sm2, s>>>(tmp, dst, k.W, k.H, radius);
-  if (nlaunch) *nlaunch += 2;
   return cudaGetLastError();
 }
 
@@ -247,10 +256,11 @@ cudaError_t launch_boxor(const KParams &k, const uint32_t *src, uint32_t *tmp, u
 // first strict minimum of H(p, d) gives the smallest H with ties to the
 // smaller disparity.  d-hat = that d if min H < ts, else d-bar_p.
 template <typename CT>
-__global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b) {
+__global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b0) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= k.W || y >= k.H) return;
+  const Buffers b = frame_view(k, b0, blockIdx.z);
   const size_t p = (size_t)y * k.W + x;
   const size_t plane = (size_t)k.W * k.H;
   const CT *cl = static_cast<const CT *>(b.censL);
@@ -273,8 +283,8 @@ __global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b) {
   b.dhat[p] = (best_d >= 0 && best_h < k.ts) ? (int16_t)best_d : b.dbar[p];
 }
 
-cudaError_t launch_semidense(const KParams &k, const Buffers &b, cudaStream_t s) {
-  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8);
+cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8, nf);
   if (k.census == 1)
     k_semidense<uint64_t><<<grid, 256, 0, s>>>(k, b);
   else
@@ -298,7 +308,8 @@ struct CostTable {
 constexpr int kCostPx = 32;
 
 template <typename CT, int DPL>
-__global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b, const __grid_constant__ CostTable tab) {
+__global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
+  const Buffers b = frame_view(k, b0, blockIdx.z);
   constexpr int Dp = 32 * DPL, G = Dp / 4;      // 4-cell words per pixel
   __shared__ CT cr_s[kCostPx + Dp];
   __shared__ CT cl_s[kCostPx];
@@ -349,8 +360,8 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b, const __grid
 }
 
 template <typename CT>
-static void launch_cost_t(const KParams &k, const Buffers &b, const CostTable &tab, cudaStream_t s) {
-  dim3 grid((k.W + kCostPx - 1) / kCostPx, k.H);
+static void launch_cost_t(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
+  dim3 grid((k.W + kCostPx - 1) / kCostPx, k.H, nf);
   switch (k.DPL) {
     case 2: k_cost<CT, 2><<<grid, 256, 0, s>>>(k, b, tab); break;
     case 4: k_cost<CT, 4><<<grid, 256, 0, s>>>(k, b, tab); break;
@@ -359,7 +370,7 @@ static void launch_cost_t(const KParams &k, const Buffers &b, const CostTable &t
   }
 }
 
-cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s) {
+cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
   CostTable tab;
   const int qs[3] = {0, k.q1, k.q2};
   for (int c = 0; c < 3; ++c)
@@ -368,9 +379,9 @@ cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s) {
       tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
     }
   if (k.census == 1)
-    launch_cost_t<uint64_t>(k, b, tab, s);
+    launch_cost_t<uint64_t>(k, b, nf, tab, s);
   else
-    launch_cost_t<uint32_t>(k, b, tab, s);
+    launch_cost_t<uint32_t>(k, b, nf, tab, s);
   return cudaGetLastError();
 }
 

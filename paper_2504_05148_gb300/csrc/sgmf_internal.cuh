@@ -1,17 +1,16 @@
 // sgmf_internal.cuh -- shared declarations of the CUDA library (sm_103a).
 //
-// Device data layout (all row-major, y outermost):
-//   images          uint8  [H][pitch]      pitched copies (pitch % 16 == 0) for TMA
-//   d-bar, d-hat    int16  [H][W]          -1 = invalid
-//   census          u32 (CS 9x7) or u64 (9x7) [H][W]
-//   presence masks  u32    [MW][H][W]      bit d of word-plane d/32 set when the
+// Device data layout (all row-major, frame outermost, then y):
+//   images          uint8  [F][H][pitch]   pitched copies (pitch % 16 == 0) for TMA
+//   d-bar, d-hat    int16  [F][H][W]       -1 = invalid
+//   census          u32 (CS 9x7) or u64 (9x7) [F][H][W]
+//   presence masks  u32    [F][MW][H][W]   bit d of word-plane d/32 set when the
 //                                           pixel's (or window's) sparse disparity is d
-//   cost C-bar      uint8  [H][W][Dp]      Dp = 32 * DPL >= D, cells d >= D hold 0
-//   partial sums    u16    [H][W][Dp]      one per line family (vertical, two diagonals)
-//   spills          uint8/u16 [line][pos][Dp]  first-direction path costs of a line
-//
-// A warp owns one SGM line; lane l holds disparities [l*DPL, (l+1)*DPL) as
-// DPL/2 words of two u16 halves (low half = even disparity).
+//   cost C-bar      uint8  [F][H][W][Dp]   Dp = 32 * DPL >= D, cells d >= D hold 0
+//   partial sums    u16    [F][H][W][Dp]   one per line family (vertical, two diagonals)
+//   spills          uint8/u16 [F][4][line][pos][Dp]  first-direction path costs of a line
+// F is the number of frames a context holds (its batch capacity); every
+// kernel takes the frame from its last grid dimension.
 #pragma once
 
 #include <cstdint>
@@ -36,7 +35,7 @@ struct KParams {
   int nbits;                  // census bits (31 or 62)
 };
 
-struct Buffers {
+struct Buffers {   // base pointers of frame 0
   uint8_t *imgL, *imgR;       // pitched copies
   int16_t *dbar, *dhat, *dstar, *dprime;
   void *censL, *censR;        // u32 or u64 per pixel
@@ -47,6 +46,35 @@ struct Buffers {
   uint16_t *dbg_sum;          // [H][W][Dp] or null
   int *err;                   // device error word
 };
+
+// per-frame element counts
+__host__ __device__ __forceinline__ size_t frame_px(const KParams &k) { return (size_t)k.W * k.H; }
+__host__ __device__ __forceinline__ size_t frame_cells(const KParams &k) { return (size_t)k.W * k.H * k.Dp; }
+
+// the buffers of frame f (spill regions hold 2-byte elements at most; the
+// kernels that use them offset by the element size they store)
+__host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const Buffers &b, int f) {
+  const size_t px = frame_px(k), cells = frame_cells(k);
+  Buffers v = b;
+  v.imgL = b.imgL + (size_t)f * k.pitch * k.H;
+  v.imgR = b.imgR + (size_t)f * k.pitch * k.H;
+  v.dbar = b.dbar + f * px;
+  v.dhat = b.dhat + f * px;
+  v.dstar = b.dstar + f * px;
+  v.dprime = b.dprime + f * px;
+  const size_t cw = k.census == 1 ? 8 : 4;
+  v.censL = static_cast<uint8_t *>(b.censL) + f * px * cw;
+  v.censR = static_cast<uint8_t *>(b.censR) + f * px * cw;
+  v.pres = b.pres + f * px * k.MW;
+  v.boxS = b.boxS + f * px * k.MW;
+  v.boxC = b.boxC + f * px * k.MW;
+  v.boxTmp = b.boxTmp + f * px * k.MW;
+  v.cost = b.cost + f * cells;
+  for (int i = 0; i < 3; ++i) v.part[i] = b.part[i] + f * cells;
+  v.spill = static_cast<uint8_t *>(b.spill) + f * 4 * cells * 2;
+  v.dbg_sum = (b.dbg_sum != nullptr && f == 0) ? b.dbg_sum : nullptr;
+  return v;
+}
 
 // ---- small device helpers ------------------------------------------------
 
@@ -116,21 +144,23 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 // ---- kernel launchers (implemented in the .cu files) -----------------------
 struct TmaMaps;   // opaque holder of the two image tensor maps (sgmf_front.cu)
 
-cudaError_t launch_ingest(const KParams &k, const Buffers &b, const uint8_t *left,
+// Every launcher covers frames [0, nf) of the context's buffers.
+cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint8_t *left,
                           const uint8_t *right, const float *lidar, cudaStream_t s);
-cudaError_t launch_census(const KParams &k, const Buffers &b, const void *tmaL, const void *tmaR,
+cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
                           cudaStream_t s);
-cudaError_t launch_boxor(const KParams &k, const uint32_t *src, uint32_t *tmp, uint32_t *dst,
-                         int radius, cudaStream_t s, int *nlaunch);
-cudaError_t launch_semidense(const KParams &k, const Buffers &b, cudaStream_t s);
-cudaError_t launch_cost(const KParams &k, const Buffers &b, cudaStream_t s);
-cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, bool spill8, cudaStream_t s);
-cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, bool spill8, cudaStream_t s);
-cudaError_t launch_consistency(const KParams &k, const Buffers &b, int16_t *out, cudaStream_t s);
+cudaError_t launch_boxor(const KParams &k, int nf, const uint32_t *src, uint32_t *tmp, uint32_t *dst,
+                         int radius, cudaStream_t s);
+cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
+cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
+cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);
 
-// host: encode the 2-D uint8 tensor map of a pitched image (driver entry point)
+// host: encode the 3-D uint8 tensor map {W, H, frames} of the pitched images
+// (driver entry point)
 int make_image_tmap(void *tmap_out /* CUtensorMap* */, const uint8_t *base, int W, int H, int pitch,
-                    int box_w, int box_h);
+                    int frames, int box_w, int box_h);
 
 // census tile geometry (shared by host map creation and the kernel)
 constexpr int kCenTileW = 64;     // output pixels per tile, x

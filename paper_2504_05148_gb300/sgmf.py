@@ -25,8 +25,9 @@ SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 
 
 # symbols declared in include/sgmf.h
 EXPORTS = (
-    "sgmf_default_params", "sgmf_create", "sgmf_set_params", "sgmf_get_params", "sgmf_set_stream",
-    "sgmf_compute", "sgmf_compute_host", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
+    "sgmf_default_params", "sgmf_create", "sgmf_create_batched", "sgmf_batch_capacity", "sgmf_set_params",
+    "sgmf_get_params", "sgmf_set_stream", "sgmf_compute", "sgmf_compute_batch", "sgmf_compute_host",
+    "sgmf_compute_host_batch", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
     "sgmf_status_string", "sgmf_set_debug", "sgmf_debug_stage", "sgmf_launches_per_compute",
     "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes",
 )
@@ -91,6 +92,10 @@ def lib(path: str | None = None):
     sig = {
         "sgmf_default_params": (None, [prm_p]),
         "sgmf_create": (i, [i, i, i, ctx_pp]),
+        "sgmf_create_batched": (i, [i, i, i, i, ctx_pp]),
+        "sgmf_batch_capacity": (i, [P]),
+        "sgmf_compute_batch": (i, [P, i, P, P, P, P]),
+        "sgmf_compute_host_batch": (i, [P, i, P, P, P, P]),
         "sgmf_set_params": (i, [P, prm_p]),
         "sgmf_get_params": (i, [P, prm_p]),
         "sgmf_set_stream": (i, [P, P]),
@@ -142,6 +147,16 @@ def sgmf_create(width: int, height: int, max_disp: int) -> int:
     return out.value
 
 
+def sgmf_create_batched(width: int, height: int, max_disp: int, max_batch: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().sgmf_create_batched(width, height, max_disp, max_batch, ctypes.byref(out)), None)
+    return out.value
+
+
+def sgmf_batch_capacity(ctx: int) -> int:
+    return lib().sgmf_batch_capacity(ctx)
+
+
 def sgmf_set_params(ctx: int, params: Params) -> None:
     c = params.to_c()
     _check(lib().sgmf_set_params(ctx, ctypes.byref(c)), ctx)
@@ -160,6 +175,16 @@ def sgmf_set_stream(ctx: int, stream: int | None) -> None:
 def sgmf_compute(ctx: int, left: int, right: int, lidar: int | None, out: int) -> None:
     """Device pointers (ints); lidar may be None."""
     _check(lib().sgmf_compute(ctx, left, right, lidar or None, out), ctx)
+
+
+def sgmf_compute_batch(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int) -> None:
+    """n frames, contiguous [n][H][W] device buffers; lidar may be None."""
+    _check(lib().sgmf_compute_batch(ctx, n, left, right, lidar or None, out), ctx)
+
+
+def sgmf_compute_host_batch(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int) -> None:
+    """n frames, contiguous [n][H][W] host buffers.  Waits for the result."""
+    _check(lib().sgmf_compute_host_batch(ctx, n, left, right, lidar or None, out), ctx)
 
 
 def sgmf_compute_host(ctx: int, left: int, right: int, lidar: int | None, out: int) -> None:
@@ -213,9 +238,10 @@ class Context:
     """Owns one sgmf context for a (width, height, max_disp) shape."""
 
     def __init__(self, width: int, height: int, max_disp: int, params: Params | None = None,
-                 stream=None):
+                 stream=None, max_batch: int = 1):
         self.W, self.H, self.D = width, height, max_disp
-        self.handle = sgmf_create(width, height, max_disp)
+        self.max_batch = max_batch
+        self.handle = sgmf_create_batched(width, height, max_disp, max_batch)
         if params is not None:
             sgmf_set_params(self.handle, params)
         if stream is not None:
@@ -228,30 +254,45 @@ class Context:
         sgmf_set_params(self.handle, params)
 
     def compute(self, left, right, lidar, out) -> None:
-        """torch CUDA tensors: uint8 (H, W) x2, float32 (H, W) or None, int16 (H, W)."""
+        """torch CUDA tensors: uint8 (H, W) or (n, H, W) x2, float32 of the same
+        shape or None, int16 of the same shape."""
+        shape = tuple(left.shape)
+        if shape == (self.H, self.W):
+            n = 1
+        elif len(shape) == 3 and shape[1:] == (self.H, self.W) and 1 <= shape[0] <= self.max_batch:
+            n = shape[0]
+        else:
+            raise ValueError(f"expected (H, W) = {(self.H, self.W)} or (n <= {self.max_batch}, H, W), got {shape}")
         for t, dt in ((left, "torch.uint8"), (right, "torch.uint8"), (out, "torch.int16")):
-            if str(t.dtype) != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (self.H, self.W):
-                raise ValueError(f"expected contiguous CUDA {dt} of shape {(self.H, self.W)}")
+            if str(t.dtype) != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"expected contiguous CUDA {dt} of shape {shape}")
         lp = None
         if lidar is not None:
             if str(lidar.dtype) != "torch.float32" or not lidar.is_cuda or not lidar.is_contiguous() \
-                    or tuple(lidar.shape) != (self.H, self.W):
-                raise ValueError("lidar must be a contiguous CUDA float32 (H, W) tensor or None")
+                    or tuple(lidar.shape) != shape:
+                raise ValueError(f"lidar must be a contiguous CUDA float32 {shape} tensor or None")
             lp = lidar.data_ptr()
-        sgmf_compute(self.handle, left.data_ptr(), right.data_ptr(), lp, out.data_ptr())
+        sgmf_compute_batch(self.handle, n, left.data_ptr(), right.data_ptr(), lp, out.data_ptr())
 
     def compute_host(self, left, right, lidar, out) -> None:
-        """numpy (or CPU torch) arrays; blocks until `out` holds the result."""
+        """numpy arrays (H, W) or (n, H, W); blocks until `out` holds the result."""
         import numpy as np
+        shape = left.shape
+        if shape == (self.H, self.W):
+            n = 1
+        elif len(shape) == 3 and shape[1:] == (self.H, self.W) and 1 <= shape[0] <= self.max_batch:
+            n = shape[0]
+        else:
+            raise ValueError(f"expected (H, W) = {(self.H, self.W)} or (n <= {self.max_batch}, H, W), got {shape}")
         for a, dt in ((left, np.uint8), (right, np.uint8), (out, np.int16)):
-            if a.dtype != dt or not a.flags["C_CONTIGUOUS"] or a.shape != (self.H, self.W):
-                raise ValueError(f"expected C-contiguous {dt} of shape {(self.H, self.W)}")
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"] or a.shape != shape:
+                raise ValueError(f"expected C-contiguous {dt} of shape {shape}")
         lp = None
         if lidar is not None:
-            if lidar.dtype != np.float32 or not lidar.flags["C_CONTIGUOUS"] or lidar.shape != (self.H, self.W):
-                raise ValueError("lidar must be C-contiguous float32 (H, W) or None")
+            if lidar.dtype != np.float32 or not lidar.flags["C_CONTIGUOUS"] or lidar.shape != shape:
+                raise ValueError(f"lidar must be C-contiguous float32 {shape} or None")
             lp = lidar.ctypes.data
-        sgmf_compute_host(self.handle, left.ctypes.data, right.ctypes.data, lp, out.ctypes.data)
+        sgmf_compute_host_batch(self.handle, n, left.ctypes.data, right.ctypes.data, lp, out.ctypes.data)
 
     def sync(self) -> None:
         sgmf_sync(self.handle)

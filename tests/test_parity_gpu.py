@@ -263,3 +263,59 @@ def test_repeated_calls_reuse_scratch(gpu):
         np.testing.assert_array_equal(res[1], oracle.compute(b.left, b.right, b.lidar, b.D, dumps=False).out)
     finally:
         ctx.close()
+
+
+def _batch_run(scs, params=None, lidar=True):
+    import torch
+    dev = torch.device("cuda:0")
+    H, W, D = scs[0].H, scs[0].W, scs[0].D
+    ctx = S.Context(W, H, D, params, max_batch=len(scs) + 1)
+    try:
+        l = torch.from_numpy(np.stack([s.left for s in scs])).to(dev)
+        r = torch.from_numpy(np.stack([s.right for s in scs])).to(dev)
+        li = torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev) if lidar else None
+        o = torch.empty((len(scs), H, W), dtype=torch.int16, device=dev)
+        ctx.compute(l, r, li, o)
+        ctx.sync()
+        return o.cpu().numpy()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("case", ["default", "dsgm", "u16_spill", "four_paths"])
+def test_batch_matches_oracle_per_frame(gpu, case):
+    params = S.Params() if case == "default" else PARAM_CASES[case]
+    scs = [scenes.tiny(1100 + i) for i in range(3)]
+    got = _batch_run(scs, params)
+    for i, s in enumerate(scs):
+        want = oracle.compute(s.left, s.right, s.lidar, s.D, _to_oracle_params(params), dumps=False).out
+        np.testing.assert_array_equal(got[i], want, err_msg=f"frame {i}")
+
+
+@pytest.mark.parametrize("W,H,D", [(71, 29, 100), (9, 7, 16), (130, 40, 200)])
+def test_batch_ragged_shapes(gpu, W, H, D):
+    scs = [scenes.random_small(5000 + i, W, H, D) for i in range(4)]
+    got = _batch_run(scs)
+    for i, s in enumerate(scs):
+        np.testing.assert_array_equal(got[i], oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out)
+
+
+def test_batch_full_size_and_host_batch(gpu):
+    """Four 1242 x 375, D = 128 frames in one batch (the benchmark launch
+    shape), through the device and the host batch entry points."""
+    scs = [scenes.kitti(2200 + i) for i in range(4)]
+    got = _batch_run(scs)
+    want = [oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out for s in scs]
+    for i in range(4):
+        np.testing.assert_array_equal(got[i], want[i])
+    ctx = S.Context(scs[0].W, scs[0].H, scs[0].D, max_batch=4)
+    try:
+        out = np.empty((4,) + scs[0].shape, np.int16)
+        ctx.compute_host(np.stack([s.left for s in scs]), np.stack([s.right for s in scs]),
+                         np.stack([s.lidar for s in scs]), out)
+        for i in range(4):
+            np.testing.assert_array_equal(out[i], want[i])
+        with pytest.raises(S.SgmfError):
+            S.sgmf_compute_batch(ctx.handle, 5, 1, 1, None, 1)
+    finally:
+        ctx.close()
