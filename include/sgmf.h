@@ -198,6 +198,35 @@ sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n
 /* Bytes of device memory the context holds. */
 size_t sgmf_device_bytes(const sgmf_ctx *c);
 
+/* The three-view consistency stage alone, without a context and without
+ * allocating anything.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory where they call it
+ * (a pool they do not own, a real-time loop that forbids cudaMalloc after
+ * start-up, a plugin host that only hands out input and output buffers).
+ *
+ * Computes D^{c*} of Eq. 6 for one width x height frame, exactly as
+ * sgmf_compute's last stage does, from caller-owned DEVICE buffers: dstar and
+ * dprime (int16 H x W, d* and d' of the frame, e.g. SGMF_STAGE_DSTAR /
+ * SGMF_STAGE_DPRIME), sparse_lidar_disp (float32 H x W, the same LiDAR map
+ * given to sgmf_compute, or NULL) and out_disp (int16 H x W).  p supplies
+ * tc, rc, lr_max_diff and consistency (validated like sgmf_set_params).
+ * Enqueued on cuda_stream (NULL = legacy default stream); returns without
+ * waiting.
+ *
+ * Working memory is one file-scope device array of 32 MiB (8 Mi 32-bit
+ * words) that every GPU loading this library holds until the process exits;
+ * a frame needs 3 * W * H * ceil(max_disp / 64) * 2 words (for max_disp <= 128
+ * about 700 000 pixels fit).  Larger frames are rejected with SGMF_ERR_SHAPE
+ * before anything is launched.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race.  No cudaMalloc, cudaFree or
+ * allocating library call is made.  Errors: SGMF_ERR_ARG, SGMF_ERR_SHAPE,
+ * SGMF_ERR_PARAM, SGMF_ERR_CUDA; the message is in sgmf_last_error(NULL). */
+sgmf_status sgmf_check_static(int width, int height, int max_disp, const sgmf_params *p,
+                              const int16_t *dstar, const int16_t *dprime,
+                              const float *sparse_lidar_disp, int16_t *out_disp, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,7 +112,7 @@ static long max_cost(const sgmf_params &p) {
   return mx;
 }
 
-static sgmf_status validate(const sgmf_params &p, std::string &why) {
+sgmf_status sgmf::validate_params(const sgmf_params &p, std::string &why) {
   char buf[256];
   auto bad = [&](const char *m) {
     why = m;
@@ -260,6 +260,8 @@ extern "C" void sgmf_destroy(sgmf_ctx *c) {
   delete c;
 }
 
+void sgmf::set_noctx_error(const std::string &msg) { g_create_err = msg; }
+
 extern "C" const char *sgmf_last_error(const sgmf_ctx *c) {
   return c ? c->err.c_str() : g_create_err.c_str();
 }
@@ -267,7 +269,7 @@ extern "C" const char *sgmf_last_error(const sgmf_ctx *c) {
 extern "C" sgmf_status sgmf_set_params(sgmf_ctx *c, const sgmf_params *p) {
   if (!c || !p) return fail(c, SGMF_ERR_ARG, "sgmf_set_params: NULL argument");
   std::string why;
-  if (validate(*p, why) != SGMF_OK) return fail(c, SGMF_ERR_PARAM, "sgmf_set_params: %s", why.c_str());
+  if (validate_params(*p, why) != SGMF_OK) return fail(c, SGMF_ERR_PARAM, "sgmf_set_params: %s", why.c_str());
   apply_params(c, *p);
   return SGMF_OK;
 }

@@ -14,7 +14,10 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+
+#include "sgmf.h"
 
 namespace sgmf {
 
@@ -156,6 +159,11 @@ cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);
+
+// host: parameter rules of sgmf_set_params (SGMF_OK or SGMF_ERR_PARAM with a reason)
+sgmf_status validate_params(const sgmf_params &p, std::string &why);
+// host: message returned by sgmf_last_error(NULL) on this thread
+void set_noctx_error(const std::string &msg);
 
 // host: encode the 3-D uint8 tensor map {W, H, frames} of the pitched images
 // (driver entry point)

@@ -29,7 +29,7 @@ EXPORTS = (
     "sgmf_get_params", "sgmf_set_stream", "sgmf_compute", "sgmf_compute_batch", "sgmf_compute_host",
     "sgmf_compute_host_batch", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
     "sgmf_status_string", "sgmf_set_debug", "sgmf_debug_stage", "sgmf_launches_per_compute",
-    "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes",
+    "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes", "sgmf_check_static",
 )
 
 
@@ -112,6 +112,7 @@ def lib(path: str | None = None):
         "sgmf_kernel_times": (i, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]),
         "sgmf_device_bytes": (sz, [P]),
+        "sgmf_check_static": (i, [i, i, i, prm_p, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -230,6 +231,14 @@ def sgmf_kernel_times(ctx: int, cap: int = 32) -> list[tuple[str, float]]:
 
 def sgmf_device_bytes(ctx: int) -> int:
     return lib().sgmf_device_bytes(ctx)
+
+
+def sgmf_check_static(width: int, height: int, max_disp: int, params: Params, dstar: int, dprime: int,
+                      lidar: int | None, out: int, stream: int | None = None) -> None:
+    """Consistency stage without a context or allocation (device pointers)."""
+    c = params.to_c()
+    _check(lib().sgmf_check_static(width, height, max_disp, ctypes.byref(c), dstar, dprime, lidar or None, out,
+                                   stream or None), None)
 
 
 # ---- torch convenience wrapper ------------------------------------------------------
