@@ -31,7 +31,7 @@ WORKLOAD = "kitti_1242x375_d128_sdsgm_8path"
 METRIC = "W*H*D/s and frames/s at 1242x375 D=128 (plain)"
 UNIT = "W*H*D/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_kitti_1242x375_d128.txt")
 
 # Algorithmic work of each kernel for V = W*H*D cells and N = W*H pixels.
 # bytes: data the stage must read and write in HBM given its inputs and outputs
@@ -119,9 +119,8 @@ class ClockSampler:
 
 
 def dist_setup(gpus: int):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2504_05148_gb300 import replicas
+    rank, world, local = replicas.rank_env()
     pg = False
     if world > 1:
         import torch.distributed as dist
@@ -131,8 +130,8 @@ def dist_setup(gpus: int):
 
 
 def make_frames(B: int, rank: int):
-    from paper_2504_05148_gb300 import scenes
-    return [scenes.kitti(2000 + rank * 1000 + i) for i in range(B)]
+    from paper_2504_05148_gb300 import replicas, scenes
+    return [scenes.kitti(sd) for sd in replicas.frame_seeds(rank, B)]
 
 
 def time_oracle(frames, budget_s: float = 12.0, max_frames: int = 8):
@@ -304,13 +303,17 @@ def main():
         t_s = avg[dom] * 1e-3
         t_hbm = alg["bytes"] / (peaks["hbm_gbs"] * 1e9)
         t_alu = alg["ops"] / alu_peak
+        # measured DRAM bytes per frame from the committed ncu summary, valid only
+        # while the kernel sources are the ones it was captured from
         traffic = None
         try:
+            cur = src_hash()
             with open(TRAFFIC_FILE) as fh:
-                tf = json.load(fh)
-            if tf.get("src_hash") == src_hash() and dom in tf.get("kernels", {}):
-                traffic = tf["kernels"][dom]["dram_bytes_per_frame"]
-        except Exception:
+                for line in fh:
+                    parts = line.split()
+                    if len(parts) == 3 and not line.startswith("#") and parts[0] == dom and parts[1] == cur:
+                        traffic = int(parts[2]) * B
+        except OSError:
             traffic = None
         if t_hbm >= t_alu:
             ach = alg["bytes"] / t_s / 1e9
