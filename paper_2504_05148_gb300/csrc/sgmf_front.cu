@@ -72,6 +72,36 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 // loads of the 96 x 22 byte boxes starting at (x0-16, y0-3): the x start is a
 // multiple of 16, and samples outside the image arrive as 0 and are masked
 // by the coordinate test on border tiles.
+// Census bits of the pixel at tile position (sx, sy): offsets are visited in
+// reverse raster order and shifted in, so offset k lands in bit k.  A bit is
+// the sign of I(q) - I(p+o) (q = p-o for the centre-symmetric kind, q = p
+// otherwise); INTERIOR tiles have every sample inside the image, elsewhere a
+// bit with a sample outside is cleared.
+template <bool FULL, bool INTERIOR>
+__device__ __forceinline__ uint64_t census_bits(const uint8_t (*T)[kCenBoxW], int sx, int sy, int x, int y, int W,
+                                                int H) {
+  uint64_t c = 0;
+  const int centre = T[sy][sx];
+#pragma unroll
+  for (int dy = 3; dy >= -3; --dy) {
+#pragma unroll
+    for (int dx = 4; dx >= -4; --dx) {
+      if (dx == 0 && dy == 0) continue;
+      if (!FULL && (dy > 0 || (dy == 0 && dx > 0))) continue;   // the half before the centre
+      const int a = T[sy + dy][sx + dx];
+      const int bq = FULL ? centre : (int)T[sy - dy][sx - dx];
+      uint32_t bit = (uint32_t)(bq - a) >> 31;                 // a > bq
+      if (!INTERIOR) {
+        bool in = (unsigned)(x + dx) < (unsigned)W && (unsigned)(y + dy) < (unsigned)H;
+        if (!FULL) in = in && (unsigned)(x - dx) < (unsigned)W && (unsigned)(y - dy) < (unsigned)H;
+        bit = in ? bit : 0u;
+      }
+      c = c + c + bit;
+    }
+  }
+  return c;
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __grid_constant__ CUtensorMap mapL,
                                                 const __grid_constant__ CUtensorMap mapR) {
@@ -104,39 +134,12 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __g
     const int y = y0 + r;
     if (x >= k.W || y >= k.H) continue;
     const int sx = tx + 16, sy = r + 3;
+    const size_t p = (size_t)y * k.W + x;
 #pragma unroll
     for (int img = 0; img < 2; ++img) {
       const uint8_t(*T)[kCenBoxW] = reinterpret_cast<const uint8_t(*)[kCenBoxW]>(tiles + img * kBoxBytes);
-      uint64_t c = 0;
-      int bit = 0;
-#pragma unroll
-      for (int dy = -3; dy <= 3; ++dy) {
-#pragma unroll
-        for (int dx = -4; dx <= 4; ++dx) {
-          if (dx == 0 && dy == 0) {
-            if (!FULL) goto done;
-            continue;
-          }
-          {
-            const uint8_t a = T[sy + dy][sx + dx];
-            bool v;
-            bool inside = true;
-            if (FULL) {
-              v = a > T[sy][sx];
-              if (!interior) inside = (unsigned)(x + dx) < (unsigned)k.W && (unsigned)(y + dy) < (unsigned)k.H;
-            } else {
-              v = a > T[sy - dy][sx - dx];
-              if (!interior)
-                inside = (unsigned)(x + dx) < (unsigned)k.W && (unsigned)(y + dy) < (unsigned)k.H &&
-                         (unsigned)(x - dx) < (unsigned)k.W && (unsigned)(y - dy) < (unsigned)k.H;
-            }
-            if (v && inside) c |= (uint64_t)1 << bit;
-            ++bit;
-          }
-        }
-      }
-    done:
-      const size_t p = (size_t)y * k.W + x;
+      const uint64_t c = interior ? census_bits<FULL, true>(T, sx, sy, x, y, k.W, k.H)
+                                  : census_bits<FULL, false>(T, sx, sy, x, y, k.W, k.H);
       if (FULL)
         static_cast<uint64_t *>(img ? b.censR : b.censL)[p] = c;
       else
@@ -187,51 +190,76 @@ int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch
 // Separable box-OR of presence masks: dst[w][y][x] = OR of src[w][y'][x'] over
 // |x'-x| <= r, |y'-y| <= r inside the image.  The OR over a clipped rectangle
 // is the OR (over rows) of the ORs along each row, so a row pass followed by
-// a column pass is exact.
+// a column pass is exact.  Each pass builds a doubling table in shared memory
+// (level j holds the OR of 2^j consecutive words); OR being idempotent, the
+// window of L = 2r+1 words is the OR of two level-k entries (2^k <= L < 2^(k+1))
+// that overlap: k + 1 ORs per word instead of L.
 constexpr int kBoxRowTile = 256;
+
+__device__ __forceinline__ int floor_log2(int v) { return 31 - __clz(v); }
 
 __global__ void __launch_bounds__(kBoxRowTile) k_boxor_rows(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                                            int W, int H, int r) {
-  extern __shared__ uint32_t seg[];
+  extern __shared__ uint32_t seg[];            // two buffers of n words
   const int y = blockIdx.y, w = blockIdx.z;
   const size_t base = ((size_t)w * H + y) * W;
   const int x0 = blockIdx.x * kBoxRowTile;
   const int n = kBoxRowTile + 2 * r;
+  uint32_t *A = seg, *B = seg + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int x = x0 - r + i;
-    seg[i] = (x >= 0 && x < W) ? src[base + x] : 0u;
+    A[i] = (x >= 0 && x < W) ? src[base + x] : 0u;
+  }
+  const int L = 2 * r + 1, k = floor_log2(L);
+  for (int j = 0; j < k; ++j) {
+    __syncthreads();
+    const int s = 1 << j;
+    for (int i = threadIdx.x; i + s < n; i += blockDim.x) B[i] = A[i] | A[i + s];
+    __syncthreads();
+    uint32_t *t = A;
+    A = B;
+    B = t;
   }
   __syncthreads();
   const int x = x0 + threadIdx.x;
   if (x >= W) return;
-  uint32_t acc = 0;
-  for (int i = 0; i <= 2 * r; ++i) acc |= seg[threadIdx.x + i];
-  dst[base + x] = acc;
+  // window [threadIdx.x, threadIdx.x + L - 1] of the segment
+  dst[base + x] = A[threadIdx.x] | A[threadIdx.x + L - (1 << k)];
 }
 
 constexpr int kBoxColW = 32, kBoxColH = 64;
 
 __global__ void __launch_bounds__(256) k_boxor_cols(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                                    int W, int H, int r) {
-  extern __shared__ uint32_t blk[];   // [(kBoxColH + 2r)][kBoxColW]
+  extern __shared__ uint32_t blk[];            // two buffers of [(kBoxColH + 2r)][kBoxColW]
   const int w = blockIdx.z;
   const size_t plane = (size_t)w * H * W;
   const int x0 = blockIdx.x * kBoxColW, y0 = blockIdx.y * kBoxColH;
   const int rows = kBoxColH + 2 * r;
-  const int tx = threadIdx.x & 31;
-  for (int i = threadIdx.x >> 5; i < rows; i += 8) {
-    const int y = y0 - r + i, x = x0 + tx;
-    blk[i * kBoxColW + tx] = (y >= 0 && y < H && x < W) ? src[plane + (size_t)y * W + x] : 0u;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  uint32_t *A = blk, *B = blk + rows * kBoxColW;
+  for (int i = ty; i < rows; i += 8) {
+    const int yy = y0 - r + i, x = x0 + tx;
+    A[i * kBoxColW + tx] = (yy >= 0 && yy < H && x < W) ? src[plane + (size_t)yy * W + x] : 0u;
+  }
+  const int L = 2 * r + 1, k = floor_log2(L);
+  for (int j = 0; j < k; ++j) {
+    __syncthreads();
+    const int s = 1 << j;
+    for (int i = ty; i + s < rows; i += 8) B[i * kBoxColW + tx] = A[i * kBoxColW + tx] | A[(i + s) * kBoxColW + tx];
+    __syncthreads();
+    uint32_t *t = A;
+    A = B;
+    B = t;
   }
   __syncthreads();
   const int x = x0 + tx;
   if (x >= W) return;
-  for (int oy = threadIdx.x >> 5; oy < kBoxColH; oy += 8) {
+  const int off = L - (1 << k);
+  for (int oy = ty; oy < kBoxColH; oy += 8) {
     const int y = y0 + oy;
     if (y >= H) break;
-    uint32_t acc = 0;
-    for (int i = 0; i <= 2 * r; ++i) acc |= blk[(oy + i) * kBoxColW + tx];
-    dst[plane + (size_t)y * W + x] = acc;
+    dst[plane + (size_t)y * W + x] = A[oy * kBoxColW + tx] | A[(oy + off) * kBoxColW + tx];
   }
 }
 
@@ -239,12 +267,16 @@ cudaError_t launch_boxor(const KParams &k, int nf, const uint32_t *src, uint32_t
                          cudaStream_t s) {
   // frames and mask words are contiguous planes: plane z = f * MW + w
   dim3 g1((k.W + kBoxRowTile - 1) / kBoxRowTile, k.H, nf * k.MW);
-  size_t sm1 = (size_t)(kBoxRowTile + 2 * radius) * sizeof(uint32_t);
+  size_t sm1 = 2 * (size_t)(kBoxRowTile + 2 * radius) * sizeof(uint32_t);
   k_boxor_rows<<<g1, kBoxRowTile, sm1, s>>>(src, tmp, k.W, k.H, radius);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 g2((k.W + kBoxColW - 1) / kBoxColW, (k.H + kBoxColH - 1) / kBoxColH, nf * k.MW);
-  size_t sm2 = (size_t)(kBoxColH + 2 * radius) * kBoxColW * sizeof(uint32_t);
+  size_t sm2 = 2 * (size_t)(kBoxColH + 2 * radius) * kBoxColW * sizeof(uint32_t);
+  if (sm2 > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    if (e != cudaSuccess) return e;
+  }
   k_boxor_cols<<<g2, 256, sm2, s>>>(tmp, dst, k.W, k.H, radius);
   return cudaGetLastError();
 }
@@ -299,8 +331,9 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 //   C-bar = floor(((b-a) H + a q + floor(b/2)) / b),  q = 0 / q1 / q2 for
 // |d - prior| = 0 / 1 / > 1, looked up in a table built on the host.
 // A CTA handles 32 pixels of one row: their right-census window is staged in
-// shared memory, and consecutive threads write consecutive 4-cell words of
-// the [x][Dp] cost rows (cells d >= D hold 0).
+// shared memory, the lanes of a warp walk the disparities of one pixel, and
+// the CTA's [32][Dp] cost rows, assembled in shared memory, leave as 16-byte
+// stores (cells d >= D hold 0).
 struct CostTable {
   uint8_t v[3][64];   // [q class][H]
 };
@@ -309,12 +342,13 @@ constexpr int kCostPx = 32;
 
 template <typename CT, int DPL>
 __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
-  const Buffers b = frame_view(k, b0, blockIdx.z);
-  constexpr int Dp = 32 * DPL, G = Dp / 4;      // 4-cell words per pixel
+  constexpr int Dp = 32 * DPL;
   __shared__ CT cr_s[kCostPx + Dp];
   __shared__ CT cl_s[kCostPx];
   __shared__ int pd_s[kCostPx];
   __shared__ uint8_t tab_s[3 * 64];
+  __shared__ __align__(16) uint8_t out_s[kCostPx * Dp];   // the block's cost rows, [x][d]
+  const Buffers b = frame_view(k, b0, blockIdx.z);
   const int x0 = blockIdx.x * kCostPx, y = blockIdx.y, W = k.W;
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
@@ -332,20 +366,20 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   }
   for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
-  uint32_t *out = reinterpret_cast<uint32_t *>(b.cost + rowp * Dp);
-  for (int j = threadIdx.x; j < kCostPx * G; j += blockDim.x) {
-    const int px = j / G, g = j - px * G;
+  // lanes walk disparities (d = lane + 32 j): the right-census reads of a warp
+  // are consecutive words, free of bank conflicts
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int npx = min(kCostPx, W - x0);
+  for (int px = warp; px < npx; px += 8) {
     const int x = x0 + px;
-    if (x >= W) break;                          // j grows with px: the rest is past the row
     const CT c = cl_s[px];
     const int pd = pd_s[px];
-    uint32_t word = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int d = 4 * g + i;
+    for (int j = 0; j < DPL; ++j) {
+      const int d = lane + 32 * j;
       uint32_t v = 0;
       if (d < k.D) {
-        const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr_s[x - d - base])) : k.nbits;
+        const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr_s[px - d + Dp - 1])) : k.nbits;
         if (pd < 0) {
           v = (uint32_t)h;
         } else {
@@ -353,10 +387,15 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
           v = tab_s[(ad == 0 ? 0 : (ad == 1 ? 64 : 128)) + h];
         }
       }
-      word |= v << (8 * i);
+      out_s[px * Dp + d] = (uint8_t)v;
     }
-    out[(size_t)x * G + g] = word;
   }
+  __syncthreads();
+  // the block's [npx][Dp] bytes are contiguous in the cost volume: 16-byte stores
+  uint4 *dst = reinterpret_cast<uint4 *>(b.cost + (rowp + x0) * Dp);
+  const uint4 *src = reinterpret_cast<const uint4 *>(out_s);
+  const int nvec = npx * Dp / 16;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
 }
 
 template <typename CT>
