@@ -59,12 +59,13 @@ class Params:
     semidense: int = 1
     consistency: int = CHECK_STEREO_LIDAR
     num_paths: int = 8
+    subpixel: int = 0
 
 
 class _CParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "p1", "p2", "q1", "q2", "alpha_num", "alpha_den", "ts", "rs", "tc", "rc",
-        "lr_max_diff", "census", "semidense", "consistency", "num_paths")]
+        "lr_max_diff", "census", "semidense", "consistency", "num_paths", "subpixel")]
 
 
 def build(force: bool = False) -> str:
@@ -99,6 +100,7 @@ def lib():
         L.sgmfo_aggregate.argtypes = [i, i, i, P, i, i, i, P]
         L.sgmfo_aggregate.restype = i
         L.sgmfo_wta.argtypes = [i, i, i, P, P, P]
+        L.sgmfo_subpixel.argtypes = [i, i, i, P, P, P]
         L.sgmfo_consistency.argtypes = [i, i, P, P, P, i, i, i, i, P]
         L.sgmfo_compute.argtypes = [ctypes.POINTER(_CParams), i, i, i, P, P, P, P,
                                     P, P, P, P, P, P, P, P]
@@ -201,6 +203,16 @@ def wta(sv: np.ndarray):
     dp = np.empty((H, W), np.int16)
     lib().sgmfo_wta(W, H, D, _p(sv), _p(ds), _p(dp))
     return ds, dp
+
+
+def subpixel(sv: np.ndarray, dstar: np.ndarray) -> np.ndarray:
+    """Sub-pixel disparity of the parabola fit (Sec. III), int16 in 1/16 px."""
+    sv = _c(sv, np.int32)
+    dstar = _c(dstar, np.int16)
+    H, W, D = sv.shape
+    out = np.empty((H, W), np.int16)
+    lib().sgmfo_subpixel(W, H, D, _p(sv), _p(dstar), _p(out))
+    return out
 
 
 def consistency(dstar, dprime, dbar, tc: int, rc: int, lr_max_diff: int = 1,

@@ -47,6 +47,7 @@ typedef struct {
     int32_t semidense;           /* 1 = SDSGM, 0 = DSGM (Table I) */
     int32_t consistency;         /* SGMFO_CHECK_* */
     int32_t num_paths;           /* 8 (Sec. III) or 4 */
+    int32_t subpixel;            /* 1: output in 1/16 px after the parabola fit (Sec. III) */
 } sgmfo_params;
 
 static int iabs_(int v) { return v < 0 ? -v : v; }
@@ -309,6 +310,36 @@ void sgmfo_wta(int W, int H, int D, const int32_t *sv, int16_t *dstar, int16_t *
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sub-pixel disparity (Sec. III, the step after Eq. 3): the parabola through
+ * (d* - 1, S(d* - 1)), (d*, S(d*)), (d* + 1, S(d* + 1)) has its vertex at
+ *   d* + (S(d* - 1) - S(d* + 1)) / (2 (S(d* - 1) - 2 S(d*) + S(d* + 1))).
+ * Readings: the result is kept in fixed point with 4 fraction bits (1/16 px),
+ * the fraction rounded half up; where d* = 0 or d* = D - 1 one neighbour is
+ * missing and the result is 16 d*.  d* being the smallest argmin, S(d* - 1)
+ * > S(d*) <= S(d* + 1): the denominator is positive and the offset lies in
+ * [-1/2, 1/2], i.e. [-8, 8] sixteenths. */
+static long floor_div_(long a, long b) /* b > 0 */
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+void sgmfo_subpixel(int W, int H, int D, const int32_t *sv, const int16_t *dstar, int16_t *dsub)
+{
+    for (size_t p = 0; p < (size_t)W * H; ++p) {
+        const int ds = dstar[p];
+        if (ds <= 0 || ds >= D - 1) {
+            dsub[p] = (int16_t)(16 * ds);
+            continue;
+        }
+        const int32_t *s = sv + p * D;
+        const long num = (long)s[ds - 1] - s[ds + 1];
+        const long den = 2 * ((long)s[ds - 1] - 2L * s[ds] + s[ds + 1]);
+        /* 16 num / den rounded half up = floor((32 num + den) / (2 den)) */
+        dsub[p] = (int16_t)(16 * ds + floor_div_(32 * num + den, 2 * den));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Stereo-LiDAR consistency check, Eq. 6 (Sec. IV-C).  d*_p is kept when
  *   the stereo term holds: the matching pixel q_m = (x - d*, y) exists and
  *   |d*_p - d'(q_m)| <= lr_max_diff (1 in Eq. 6), or
@@ -352,8 +383,10 @@ void sgmfo_consistency(int W, int H, const int16_t *dstar, const int16_t *dprime
 
 /* ------------------------------------------------------------------------ */
 /* The whole pipeline of Fig. 1: semidensification (optional, Table I),
- * SGM with DDC, WTA, three-view check.  Every non-NULL dump pointer receives
- * the corresponding intermediate.  Returns 0, or -1 on allocation failure. */
+ * SGM with DDC, WTA, three-view check.  With prm->subpixel the pixels that
+ * pass the check carry the sub-pixel disparity in 1/16 px instead of d*
+ * (invalid stays -1).  Every non-NULL dump pointer receives the
+ * corresponding intermediate.  Returns 0, or -1 on allocation failure. */
 int sgmfo_compute(const sgmfo_params *prm, int W, int H, int D,
                   const uint8_t *left, const uint8_t *right, const float *lidar,
                   int16_t *out,
@@ -388,6 +421,14 @@ int sgmfo_compute(const sgmfo_params *prm, int W, int H, int D,
     sgmfo_wta(W, H, D, hv, dstar, dprime);
     sgmfo_consistency(W, H, dstar, dprime, dbar, prm->tc, prm->rc, prm->lr_max_diff,
                       prm->consistency, out);
+    if (prm->subpixel) {
+        int16_t *dsub = (int16_t *)malloc(n * sizeof(int16_t));
+        if (!dsub) goto out;
+        sgmfo_subpixel(W, H, D, hv, dstar, dsub);
+        for (size_t p = 0; p < n; ++p)
+            if (out[p] != SGMFO_INVALID) out[p] = dsub[p];
+        free(dsub);
+    }
     if (dump_dbar) memcpy(dump_dbar, dbar, n * sizeof(int16_t));
     if (dump_cl) memcpy(dump_cl, cl, n * sizeof(uint64_t));
     if (dump_cr) memcpy(dump_cr, cr, n * sizeof(uint64_t));

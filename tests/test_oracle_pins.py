@@ -281,6 +281,80 @@ def test_right_view_diagonal_closed_form():
 
 
 # ---------------------------------------------------------------------------
+# Sub-pixel parabola fit (Sec. III, after Eq. 3); results in 1/16 px
+
+def test_subpixel_recovers_the_vertex_of_a_sampled_parabola():
+    """S sampled from a (16 d - V)^2 + c: the parabola through three samples is
+    that parabola, so its vertex V / 16 comes back exactly, also when V / 16 is
+    a half-integer (then d* and d* + 1 tie and d* is the smaller)."""
+    rng = np.random.default_rng(31)
+    W, D = 300, 24
+    d = np.arange(D)
+    V = rng.integers(24, 16 * (D - 2) + 1, size=W)
+    a = rng.integers(1, 4, size=W)
+    c = rng.integers(0, 50, size=W)
+    S = (a[:, None] * (16 * d[None, :] - V[:, None]) ** 2 + c[:, None]).astype(np.int32)[None]
+    ds, _ = oracle.wta(S)
+    assert ((ds >= 1) & (ds <= D - 2)).all()
+    np.testing.assert_array_equal(oracle.subpixel(S, ds)[0], V)
+
+
+def test_subpixel_hand_values():
+    # (S(d*-1), S(d*), S(d*+1)) -> offset 16 (S- - S+) / (2 (S- - 2 S* + S+)), rounded half up
+    cases = [((5, 3, 3), 8),        # tie with d* + 1: the vertex is half-way
+             ((17, 0, 15), 1),      # 32 / 64 = 0.5 sixteenths -> 1
+             ((15, 0, 17), 0),      # -0.5 -> 0
+             ((9, 1, 9), 0),        # symmetric
+             ((40, 0, 8), 5),       # 16 * 32 / 96 = 5.33 -> 5
+             ((8, 0, 40), -5),      # -5.33 -> -5
+             ((2, 0, 200), -8)]     # 16 * -198 / 404 = -7.84 -> -8
+    for (sm, s0, sp), want in cases:
+        S = np.array([[[999, sm, s0, sp, 999]]], np.int32)
+        ds, _ = oracle.wta(S)
+        assert ds[0, 0] == 2
+        assert oracle.subpixel(S, ds)[0, 0] == 32 + want, (sm, s0, sp)
+
+
+def test_subpixel_at_the_ends_of_the_range_is_integer():
+    S = np.array([[[0, 5, 9, 9], [9, 9, 5, 1], [4, 4, 4, 4]]], np.int32)
+    ds, _ = oracle.wta(S)
+    np.testing.assert_array_equal(ds, [[0, 3, 0]])
+    np.testing.assert_array_equal(oracle.subpixel(S, ds), [[0, 48, 0]])
+
+
+def test_subpixel_mirror_and_bounds():
+    """Reversing the disparity axis mirrors the vertex: the two results add up
+    to 16 (D - 1), plus 1 where the offset is an exact half (rounded up both
+    times); every offset lies within half a pixel of d*."""
+    rng = np.random.default_rng(32)
+    H, W, D = 3, 200, 16
+    S = rng.permutation(H * W * D).reshape(H, W, D).astype(np.int32)   # distinct values: no ties
+    ds, _ = oracle.wta(S)
+    got = oracle.subpixel(S, ds).astype(int)
+    R = np.ascontiguousarray(S[:, :, ::-1])
+    dr, _ = oracle.wta(R)
+    np.testing.assert_array_equal(dr, D - 1 - ds)
+    rev = oracle.subpixel(R, dr).astype(int)
+    tot = got + rev - 16 * (D - 1)
+    assert set(np.unique(tot)) <= {0, 1}
+    inner = (ds > 0) & (ds < D - 1)
+    assert (np.abs(got - 16 * ds.astype(int))[inner] <= 8).all()
+    assert (got[~inner] == 16 * ds[~inner]).all()
+
+
+def test_subpixel_pipeline_keeps_the_integer_check():
+    """With the fit switched on, the check (on integer d*) keeps the same
+    pixels, and each kept value lies within half a pixel of d*."""
+    s = scenes.tiny(1400)
+    r0 = oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False)
+    r1 = oracle.compute(s.left, s.right, s.lidar, s.D, oracle.Params(subpixel=1), dumps=False)
+    np.testing.assert_array_equal(r1.out < 0, r0.out < 0)
+    v = r0.out >= 0
+    assert (np.abs(r1.out[v].astype(int) - 16 * r0.out[v].astype(int)) <= 8).all()
+    assert (r1.out[v] != 16 * r0.out[v]).mean() > 0.5
+
+
+# ---------------------------------------------------------------------------
 # Semidensification (Eq. 5) hand cases
 
 def test_semidense_hand_cases():
