@@ -76,6 +76,11 @@ typedef struct {
     int32_t semidense;            /* 1 = SDSGM, 0 = DSGM (Table I) */
     int32_t consistency;          /* SGMF_CHECK_* (SGMF_CHECK_STEREO_LIDAR) */
     int32_t num_paths;            /* 8 (Sec. III) or 4 (horizontal + vertical) */
+    int32_t subpixel;             /* 0 (default): out_disp holds integer d*; 1: pixels that pass the
+                                     check hold the parabola-fit disparity of Sec. III (after Eq. 3)
+                                     in 1/16 px, i.e. 16 d* + round-half-up(16 (S(d*-1) - S(d*+1)) /
+                                     (2 (S(d*-1) - 2 S(d*) + S(d*+1)))), and 16 d* where d* = 0 or
+                                     D - 1; invalid stays -1 */
 } sgmf_params;
 
 /* Intermediate maps that sgmf_debug_stage() can copy out (test use). */
@@ -87,7 +92,8 @@ enum {
     SGMF_STAGE_COST = 4,     /* uint8 H x W x D: joint cost C-bar of Eq. 4 */
     SGMF_STAGE_SUM = 5,      /* uint16 H x W x D: S = sum_r L_r; only after sgmf_set_debug(c, 1) */
     SGMF_STAGE_DSTAR = 6,    /* int16 H x W: d* of Eq. 3 */
-    SGMF_STAGE_DPRIME = 7    /* int16 H x W: d' of the right view (diagonal search) */
+    SGMF_STAGE_DPRIME = 7,   /* int16 H x W: d' of the right view (diagonal search) */
+    SGMF_STAGE_DSUB = 8      /* int16 H x W: sub-pixel disparity in 1/16 px; only with subpixel = 1 */
 };
 
 /* Fill *p with Table II of the paper (and the documented readings). */
@@ -209,7 +215,8 @@ size_t sgmf_device_bytes(const sgmf_ctx *c);
  * dprime (int16 H x W, d* and d' of the frame, e.g. SGMF_STAGE_DSTAR /
  * SGMF_STAGE_DPRIME), sparse_lidar_disp (float32 H x W, the same LiDAR map
  * given to sgmf_compute, or NULL) and out_disp (int16 H x W).  p supplies
- * tc, rc, lr_max_diff and consistency (validated like sgmf_set_params).
+ * tc, rc, lr_max_diff and consistency (validated like sgmf_set_params;
+ * subpixel must be 0: the output is the integer d* or -1).
  * Enqueued on cuda_stream (NULL = legacy default stream); returns without
  * waiting.
  *

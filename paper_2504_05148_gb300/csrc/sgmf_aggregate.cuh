@@ -1,0 +1,857 @@
+// sgmf_aggregate.cuh -- SGM path aggregation (Eq. 2), path sum and WTA (Eq. 3).
+//
+// Kernel templates; sgmf_agg_cpl*.cu instantiate them per lane width (one
+// translation unit each, compiled in parallel) and sgmf_aggregate.cu picks
+// the instantiation for a context.
+//
+// Lines.  Each of the eight directions of Sec. III runs along a family of
+// lines; a line is walked once in each of its two directions:
+//   family 0 (vertical)      line k = column k            down: r=(0,1)   up: r=(0,-1)
+//   family 1 (diagonal)      line k: x = (k + y) mod W    down: r=(1,1)   up: r=(-1,-1)
+//   family 2 (anti-diagonal) line k: x = (k - y) mod W    down: r=(-1,1)  up: r=(1,-1)
+//   rows                     line = row y                 left->right r=(1,0), right->left r=(-1,0)
+// With the modulo every diagonal line has exactly H pixels, and a path
+// (re)starts where the line wraps, i.e. where p - r leaves the image.
+//
+// Lanes.  A group of 16 lanes (half a warp) walks one line; lane j of the
+// group holds disparities [j*CPL, (j+1)*CPL) (CPL = Dp/16 cells) as CPL/2
+// u16x2 words.  One step of Eq. 2 on a word:
+//   t     = viaddmin(vimin3(L(d-1), L(d+1), m + P2 - P1), P1, L(d))
+//         = min{ L(d), L(d-1)+P1, L(d+1)+P1, m+P2 }
+//   L'(d) = t + C(d) - m                      (one 32-bit add: t >= m per half)
+// L(d-1), L(d+1) of the two halves come from byte permutes of neighbouring
+// words (and one 16-wide shuffle each way across lanes); m = min_k L(k) is a
+// per-lane u16x2 min followed by one __reduce_min_sync over the group.  A path
+// start is the same step applied to an all-zero previous vector (with m = 0
+// it yields L = C).  Disparities beyond D are padding: their cost is raised
+// by kInf so they never reach the min.
+//
+// Data movement.  Every warp streams its inputs through a private ring of
+// shared-memory stages filled by 1-D bulk copies (cp.async.bulk, completion
+// on one mbarrier per stage) several steps ahead of the recursion, so the
+// sequential walk does not wait on global-memory latency.
+//
+// Sums.  The line kernel writes, per family, the pair sum L_down + L_up
+// (u16) of each pixel.  The row kernel adds the two row directions and the
+// family sums into S = sum_r L_r, takes d* (Eq. 3) with one group min per
+// pixel, and d' (the disparity of the right view) with a systolic running
+// min: the best key of right pixel x' = x - d moves one disparity slot per
+// step, so after D steps it has seen S(x'+d, d) for every d.
+#pragma once
+#include <cstdint>
+
+#include "sgmf_internal.cuh"
+
+namespace sgmf {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- lane-vector access (shared or global memory, generic pointers) ------------
+// CPL u8 cells at p -> CPL/2 u16x2 words; z[j] holds the pad bytes (0x40 for
+// d >= D) of cells 4j..4j+3, which become the high bytes.
+template <int CPL>
+__device__ __forceinline__ void unpack_u8(const uint8_t *p, const uint32_t (&z)[CPL / 4], uint32_t (&w)[CPL / 2]) {
+  uint32_t v[CPL / 4];
+  if constexpr (CPL == 4) {
+    v[0] = *reinterpret_cast<const uint32_t *>(p);
+  } else if constexpr (CPL == 8) {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  } else if constexpr (CPL == 12) {
+    const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
+    v[0] = q[0];
+    v[1] = q[1];
+    v[2] = q[2];
+  } else {
+    const uint4 t = *reinterpret_cast<const uint4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+#pragma unroll
+  for (int j = 0; j < CPL / 4; ++j) {
+    w[2 * j] = prmt(v[j], z[j], 0x5140);
+    w[2 * j + 1] = prmt(v[j], z[j], 0x7362);
+  }
+}
+
+// CPL/2 u16x2 words -> CPL u8 cells (every real value is <= 255 when used)
+template <int CPL>
+__device__ __forceinline__ void store_u8(uint8_t *p, const uint32_t (&w)[CPL / 2]) {
+  uint32_t v[CPL / 4];
+#pragma unroll
+  for (int j = 0; j < CPL / 4; ++j) v[j] = prmt(w[2 * j], w[2 * j + 1], 0x6420);
+  if constexpr (CPL == 4) {
+    *reinterpret_cast<uint32_t *>(p) = v[0];
+  } else if constexpr (CPL == 8) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+  } else if constexpr (CPL == 12) {
+    uint32_t *q = reinterpret_cast<uint32_t *>(p);
+    q[0] = v[0];
+    q[1] = v[1];
+    q[2] = v[2];
+  } else {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <int CPL>
+__device__ __forceinline__ void load_u16(const uint16_t *p, uint32_t (&w)[CPL / 2]) {
+  if constexpr (CPL == 4) {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    w[0] = t.x;
+    w[1] = t.y;
+  } else if constexpr (CPL == 12) {
+    const uint2 *q = reinterpret_cast<const uint2 *>(p);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint2 t = q[j];
+      w[2 * j] = t.x;
+      w[2 * j + 1] = t.y;
+    }
+  } else {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int j = 0; j < CPL / 8; ++j) {
+      const uint4 t = q[j];
+      w[4 * j] = t.x;
+      w[4 * j + 1] = t.y;
+      w[4 * j + 2] = t.z;
+      w[4 * j + 3] = t.w;
+    }
+  }
+}
+
+template <int CPL>
+__device__ __forceinline__ void store_u16(uint16_t *p, const uint32_t (&w)[CPL / 2]) {
+  if constexpr (CPL == 4) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+  } else if constexpr (CPL == 12) {
+    uint2 *q = reinterpret_cast<uint2 *>(p);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) q[j] = make_uint2(w[2 * j], w[2 * j + 1]);
+  } else {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int j = 0; j < CPL / 8; ++j) q[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  }
+}
+
+// spilled first-direction costs: u8 when every real cost fits, else u16
+template <int CPL, bool S8>
+__device__ __forceinline__ void spill_put(uint8_t *p, const uint32_t (&w)[CPL / 2]) {
+  if constexpr (S8)
+    store_u8<CPL>(p, w);
+  else
+    store_u16<CPL>(reinterpret_cast<uint16_t *>(p), w);
+}
+
+template <int CPL, bool S8>
+__device__ __forceinline__ void spill_get(const uint8_t *p, uint32_t (&w)[CPL / 2]) {
+  if constexpr (S8) {
+    const uint32_t z[CPL / 4] = {};
+    unpack_u8<CPL>(p, z, w);
+  } else {
+    load_u16<CPL>(reinterpret_cast<const uint16_t *>(p), w);
+  }
+}
+
+// ---- the recursion -----------------------------------------------------------
+struct StepConsts {
+  uint32_t p1x2;   // P1 in both halves
+  uint32_t dpx2;   // (P2 - P1) in both halves
+};
+
+// One step of Eq. 2 for the lane's words.  mm = min_k L(p - r, k) in both
+// halves; edge_lo / edge_hi are all-ones on the first / last lane of the
+// group so that the missing neighbours L(-1) and L(Dp) read as 0xffff (they
+// only enter a min).
+template <int NW>
+__device__ __forceinline__ void sgm_step(uint32_t (&L)[NW], const uint32_t (&C)[NW], uint32_t mm,
+                                         const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi) {
+  const uint32_t cap = mm + sc.dpx2;           // m + P2 - P1 per half
+  const uint32_t negmm = 0u - mm;
+  const uint32_t prev = __shfl_up_sync(kFull, L[NW - 1], 1, 16) | edge_lo;
+  const uint32_t next = __shfl_down_sync(kFull, L[0], 1, 16) | edge_hi;
+  uint32_t sh[NW + 1];
+  sh[0] = prmt(prev, L[0], 0x5432);
+#pragma unroll
+  for (int i = 1; i < NW; ++i) sh[i] = prmt(L[i - 1], L[i], 0x5432);
+  sh[NW] = prmt(L[NW - 1], next, 0x5432);
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const uint32_t t = __viaddmin_u16x2(__vimin3_u16x2(sh[i], sh[i + 1], cap), sc.p1x2, L[i]);
+    L[i] = t + C[i] + negmm;
+  }
+}
+
+// Min of a u32 over each 16-lane group: two full-warp reductions, each with
+// the other group's lanes contributing all-ones (a reduction over half a warp
+// costs far more than two over the whole warp).
+__device__ __forceinline__ uint32_t group_reduce_min(uint32_t v, int grp) {
+  const uint32_t lo = __reduce_min_sync(kFull, grp ? 0xffffffffu : v);
+  const uint32_t hi = __reduce_min_sync(kFull, grp ? v : 0xffffffffu);
+  return grp ? hi : lo;
+}
+
+// min over the group's disparities, returned in both halves
+template <int NW>
+__device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NW], int grp) {
+  uint32_t v = L[0];
+#pragma unroll
+  for (int i = 1; i + 1 < NW; i += 2) v = __vimin3_u16x2(v, L[i], L[i + 1]);
+  if constexpr (NW % 2 == 0) v = __vminu2(v, L[NW - 1]);
+  v = __vminu2(v, prmt(v, v, 0x1032));
+  return group_reduce_min(v, grp);
+}
+
+// pad bytes (0x40 = high byte of kInf) of the lane's cells d >= D
+template <int CPL>
+__device__ __forceinline__ void pad_bytes(int D, int lig, uint32_t (&z)[CPL / 4]) {
+#pragma unroll
+  for (int i = 0; i < CPL / 4; ++i) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (lig * CPL + 4 * i + j >= D) v |= 0x40u << (8 * j);
+    z[i] = v;
+  }
+}
+
+// Bounded wait for ring fill g (stage g % S, phase g / S).  The decision is
+// warp-uniform.  On a timeout the warp flags the error, gives every fill it
+// has issued (g .. issued-1) a second bounded wait, and reports false so that
+// the caller returns.
+template <int S>
+__device__ __forceinline__ bool ring_wait(uint64_t *bars, int g, int issued, int *err) {
+  const bool ok = mbar_wait_bounded(&bars[g % S], (uint32_t)(g / S) & 1u, kWaitLimit);
+  if (__all_sync(kFull, ok)) return true;
+  if ((threadIdx.x & 31) == 0) set_error(err, kErrTimeout);
+  for (int h = g; h < issued; ++h) mbar_wait_bounded(&bars[h % S], (uint32_t)(h / S) & 1u, kWaitLimit);
+  return false;
+}
+
+// ---- vertical and diagonal families -------------------------------------------
+struct LineArgs {
+  KParams k;
+  const uint8_t *cost;
+  uint16_t *part[3];
+  void *spill;            // [3][W][H][Dp] elements
+  int *err;
+  StepConsts sc;
+};
+
+template <int CPL, bool S8, int NWARP>
+struct LineCfg {
+  static constexpr int Dp = 16 * CPL;
+  static constexpr int K = CPL <= 8 ? 8 : 4;   // rows per stage
+  static constexpr int S = 3;                  // stages per warp
+  static constexpr int SB = S8 ? 1 : 2;        // spill bytes per cell
+  static constexpr int kCost = K * 2 * Dp;     // [row][line of the warp][Dp]
+  static constexpr int kSpillLine = K * Dp * SB;
+  static constexpr int kStage = kCost + 2 * kSpillLine;
+  static constexpr int kWarp = S * kStage;
+  static constexpr int kWarps = NWARP;         // warps (two lines each) per CTA: a tuning choice
+  static constexpr int kSmem = kWarps * kWarp + kWarps * S * 8;
+};
+
+// x of line k at row y in family fam
+__device__ __forceinline__ int line_x(int fam, int k, int y, int W) {
+  if (fam == 0) return k;
+  int x = (fam == 1 ? k + y : k - y) % W;
+  return x < 0 ? x + W : x;
+}
+
+// One chunk of n rows of a line walk (both lines of the warp).  DOWN: rows
+// in increasing y, the path costs are spilled; up: rows in decreasing y, the
+// spilled L_down of the row is added and the pair sum stored.  FAST: no path
+// restarts inside the chunk (known from the warp-wide min of `togo`).
+template <int CPL, bool S8, int FAM, bool DOWN, bool FAST>
+__device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *sstl, int n, uint32_t (&L)[CPL / 2],
+                                           uint32_t &mm, int &togo, int &next_len, int seg_full,
+                                           uint8_t *&sp, uint16_t *&pp, const uint32_t (&z)[CPL / 4],
+                                           const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp,
+                                           bool active, int y_hi, int y_first, int W, uint16_t *part_lane) {
+  constexpr int NW = CPL / 2, Dp = 16 * CPL, SB = S8 ? 1 : 2;
+  // partial-sum pointer step moving up one row (x - 1, x, x + 1 for families 1, 0, 2)
+  constexpr int kDelta = FAM == 0 ? 0 : (FAM == 1 ? -1 : 1);
+  const ptrdiff_t up_step = (ptrdiff_t)(kDelta - W) * Dp;
+  uint32_t C[NW];
+#pragma unroll 2
+  for (int i = 0; i < n; ++i) {
+    const int r = DOWN ? i : n - 1 - i;       // stage rows are in increasing y
+    unpack_u8<CPL>(stl + r * 2 * Dp, z, C);
+    if (!FAST) {
+      const bool start = togo == 0;
+      const uint32_t keep = start ? 0u : 0xffffffffu;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) L[w] &= keep;
+      mm &= keep;
+      if (start) {
+        togo = next_len;
+        next_len = seg_full;
+        // going up, a diagonal line restarts (after its first pixel) where x
+        // wrapped around: x = W-1 for family 1, x = 0 for family 2
+        if (!DOWN && FAM != 0) {
+          const int y = y_hi - i;
+          if (y != y_first) pp = part_lane + (size_t)(y * W + (FAM == 1 ? W - 1 : 0)) * Dp;
+        }
+      }
+      --togo;
+    }
+    sgm_step<NW>(L, C, mm, sc, edge_lo, edge_hi);
+    mm = group_min<NW>(L, grp);
+    if (DOWN) {
+      if (active) spill_put<CPL, S8>(sp, L);
+      sp += Dp * SB;
+    } else {
+      uint32_t Ld[NW];
+      spill_get<CPL, S8>(sstl + r * Dp * SB, Ld);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) Ld[w] += L[w];
+      if (active) store_u16<CPL>(pp, Ld);
+      pp += up_step;
+    }
+  }
+  if (FAST) togo -= n;
+}
+
+template <int CPL, bool S8, int FAM, int NWARP>
+__global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant__ LineArgs a) {
+  using CF = LineCfg<CPL, S8, NWARP>;
+  constexpr int NW = CPL / 2, K = CF::K, S = CF::S, Dp = CF::Dp, SB = CF::SB;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane >> 4, lig = lane & 15;
+  const int f = blockIdx.y;
+  const int W = a.k.W, H = a.k.H;
+  const size_t fcells = frame_cells(a.k);
+  const uint8_t *cost = a.cost + f * fcells;
+  uint16_t *part = a.part[FAM] + f * fcells;
+  const int line0 = (blockIdx.x * CF::kWarps + warp) * 2;
+  if (line0 >= W) return;                    // warps are independent: no block barrier below
+  const int line = line0 + grp;
+  const bool active = line < W;              // the second group of the last warp may idle
+  const int nact = line0 + 1 < W ? 2 : 1;
+  uint8_t *ring = smem + warp * CF::kWarp;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + CF::kWarps * CF::kWarp) + warp * S;
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  uint32_t z[CPL / 4];
+  pad_bytes<CPL>(a.k.D, lig, z);
+  const uint32_t edge_lo = lig == 0 ? 0xffffffffu : 0u, edge_hi = lig == 15 ? 0xffffffffu : 0u;
+  const StepConsts sc = a.sc;
+  uint8_t *spill = static_cast<uint8_t *>(a.spill) + f * 4 * fcells * 2;   // this frame's spill regions
+  const size_t spill0 = ((size_t)FAM * W + line0) * (size_t)H * Dp;     // elements, line0
+  const size_t spill_line = spill0 + (size_t)grp * H * Dp;
+  const int nch = (H + K - 1) / K;
+  auto issue = [&](int g) {
+    const bool up = g >= nch;
+    const int c = up ? g - nch : g;
+    const int stage = g % S;
+    uint8_t *st = ring + stage * CF::kStage;
+    int y_lo, n;
+    if (!up) {
+      y_lo = c * K;
+      n = min(K, H - y_lo);
+    } else {
+      const int y_hi = H - 1 - c * K;
+      y_lo = max(0, y_hi - K + 1);
+      n = y_hi - y_lo + 1;
+    }
+    if (lane == 0) mbar_expect_tx(&bars[stage], (uint32_t)(nact * n * Dp * (up ? 1 + SB : 1)));
+    __syncwarp();
+    const int r = lane >> 1, gg = lane & 1;
+    if (r < n && line0 + gg < W) {
+      const int y = y_lo + r;
+      bulk_g2s(st + (r * 2 + gg) * Dp, cost + ((size_t)y * W + line_x(FAM, line0 + gg, y, W)) * Dp, Dp,
+               &bars[stage]);
+    }
+    if (up && lane >= 30 && line0 + (lane - 30) < W) {
+      const int l = lane - 30;
+      bulk_g2s(st + CF::kCost + l * CF::kSpillLine,
+               spill + (spill0 + (size_t)l * H * Dp + (size_t)y_lo * Dp) * SB, (uint32_t)(n * Dp * SB),
+               &bars[stage]);
+    }
+  };
+
+  uint32_t L[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) L[w] = 0;
+  uint32_t mm = 0;
+  // Path restarts: togo = steps until the next restart (0: this step restarts).
+  const int x_top = line_x(FAM, line, 0, W), x_bot = line_x(FAM, line, H - 1, W);
+  const int seg_full = FAM == 0 ? 0x7fffffff : W;
+  const int cost_off = grp * Dp + lig * CPL;                          // lane's cells in a stage row
+  const int spill_off = CF::kCost + grp * CF::kSpillLine + lig * CPL * SB;
+  // ---- down: r = (0,1), (1,1), (-1,1) ----
+  int togo = 0;
+  int next_len = FAM == 0 ? 0x7fffffff : (FAM == 1 ? W - x_top : x_top + 1);
+  {
+    uint8_t *sp = spill + (spill_line + (size_t)lig * CPL) * SB;
+    uint16_t *pp = nullptr;
+    int issued = 0;
+    for (int c = 0; c < nch; ++c) {
+      while (issued < nch && issued < c + S) issue(issued++);
+      if (!ring_wait<S>(bars, c, issued, a.err)) return;
+      const int n = min(K, H - c * K);
+      const uint8_t *st = ring + (c % S) * CF::kStage;
+      const bool fast = __reduce_min_sync(kFull, (unsigned)(active ? togo : 0x7fffffff)) >= (unsigned)n;
+      if (fast)
+        line_chunk<CPL, S8, FAM, true, true>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full, sp,
+                                             pp, z, sc, edge_lo, edge_hi, grp, active, c * K + n - 1, H - 1, W, part);
+      else
+        line_chunk<CPL, S8, FAM, true, false>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full, sp,
+                                              pp, z, sc, edge_lo, edge_hi, grp, active, c * K + n - 1, H - 1, W, part);
+      __syncwarp();
+    }
+  }
+  // the spilled L_down rows are read back by bulk copies (async proxy)
+  fence_proxy_async_global();
+  __syncwarp();
+  // ---- up: r = (0,-1), (-1,-1), (1,-1); emit L_down + L_up ----
+  togo = 0;
+  next_len = FAM == 0 ? 0x7fffffff : (FAM == 1 ? x_bot + 1 : W - x_bot);
+  {
+    uint8_t *sp = nullptr;
+    uint16_t *part_lane = part + lig * CPL;
+    uint16_t *pp = part_lane + (size_t)((H - 1) * W + x_bot) * Dp;
+    int issued = nch;
+    for (int c = 0; c < nch; ++c) {
+      const int g = nch + c;
+      while (issued < 2 * nch && issued < g + S) issue(issued++);
+      if (!ring_wait<S>(bars, g, issued, a.err)) return;
+      const int y_hi = H - 1 - c * K, n = y_hi - max(0, y_hi - K + 1) + 1;
+      const uint8_t *st = ring + (g % S) * CF::kStage;
+      const bool fast = __reduce_min_sync(kFull, (unsigned)(active ? togo : 0x7fffffff)) >= (unsigned)n;
+      if (fast)
+        line_chunk<CPL, S8, FAM, false, true>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full,
+                                              sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi, H - 1, W, part_lane);
+      else
+        line_chunk<CPL, S8, FAM, false, false>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full,
+                                               sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi, H - 1, W, part_lane);
+      __syncwarp();
+    }
+  }
+}
+
+// ---- rows, path sum and WTA ----------------------------------------------------
+// One warp per image row.  Group 0 walks left -> right (r = (1,0)), group 1
+// right -> left (r = (-1,0)), in lockstep.  Each group spills its path costs
+// for the half of the row it reaches first (group 0: x < xm, group 1:
+// x >= xm); on the half it reaches second it reads the other group's spill,
+// adds the line-family sums into S, and takes d* and d' there.  For odd W
+// group 0 starts one step late so that both first halves end together.  The
+// right-view keys of pixels x' whose diagonal crosses xm are merged in shared
+// memory at the end.
+struct RowArgs {
+  KParams k;
+  const uint8_t *cost;
+  const uint16_t *part[3];
+  void *spill;            // frame 0 spill regions; the row region is the fourth
+  int16_t *dstar, *dprime;
+  int16_t *dsub;          // sub-pixel output (1/16 px), or null when the fit is off
+  uint16_t *dbg_sum;
+  int *err;
+  StepConsts sc;
+};
+
+template <int CPL, bool S8>
+struct RowCfg {
+  static constexpr int Dp = 16 * CPL;
+  static constexpr int K = CPL <= 8 ? 4 : 2;    // walk steps per stage
+  static constexpr int S = 3;
+  static constexpr int SB = S8 ? 1 : 2;
+  static constexpr int kCost = K * Dp;
+  static constexpr int kSpill = K * Dp * SB;
+  static constexpr int kPart = K * Dp * 2;
+  static constexpr int kGroup = kCost + kSpill + 3 * kPart;   // per group and stage
+  static constexpr int kStage = 2 * kGroup;
+  static constexpr int kSmem = S * kStage + S * 8 + kMaxDisp * 4;
+};
+
+// per-warp state of the row walk
+template <int CPL>
+struct RowWalk {
+  uint32_t L[CPL / 2];
+  uint32_t mm;
+  uint32_t acc[CPL];      // right-view keys; slot d holds right pixel x - d
+};
+
+struct RowGeom {
+  int W, D, xm, delay, mbase, lastLig, lastSlot;
+  bool fwd;
+  size_t row;
+};
+
+// one chunk of lockstep steps [t_lo, t_hi); SECOND: the half where S is formed;
+// RESTART: the chunk holds the first step of a walk
+template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART>
+__device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, const uint8_t *stg, int xl, int t_lo,
+                                          int t_hi, const uint32_t (&z)[CPL / 4], const uint32_t (&kb)[CPL / 2],
+                                          const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp, int lig,
+                                          uint8_t *spill_lane, int16_t *dstar, int16_t *dprime, int16_t *dsub,
+                                          uint16_t *dbg_lane, uint32_t *merge) {
+  using CF = RowCfg<CPL, S8>;
+  constexpr int NW = CPL / 2, Dp = CF::Dp, SB = CF::SB;
+  const uint8_t *cst = stg + lig * CPL;
+  const uint8_t *sst = stg + CF::kCost + lig * CPL * SB;
+  const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * 2;
+  for (int t = t_lo; t < t_hi; ++t) {
+    const int x = g.fwd ? t - g.delay : g.W - 1 - t;
+    const bool valid = x >= 0 && x < g.W;
+    const int r = valid ? x - xl : 0;
+    uint32_t C[NW];
+    unpack_u8<CPL>(cst + r * Dp, z, C);
+    if (RESTART) {
+      // a walk starts at x = 0 (group 0) / x = W-1 (group 1): zero previous vector
+      const uint32_t keep = x == (g.fwd ? 0 : g.W - 1) ? 0u : 0xffffffffu;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) w.L[i] &= keep;
+      w.mm &= keep;
+    }
+    sgm_step<NW>(w.L, C, w.mm, sc, edge_lo, edge_hi);
+    w.mm = group_min<NW>(w.L, grp);
+    if (!SECOND) {
+      if (valid) spill_put<CPL, S8>(spill_lane + (size_t)x * Dp * SB, w.L);
+      continue;
+    }
+    uint32_t Sm[NW];
+    spill_get<CPL, S8>(sst + r * Dp * SB, Sm);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) Sm[i] += w.L[i];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      uint32_t T[NW];
+      load_u16<CPL>(reinterpret_cast<const uint16_t *>(pst + j * CF::kPart + r * Dp * 2), T);
+#pragma unroll
+      for (int i = 0; i < NW; ++i) Sm[i] += T[i];
+    }
+    if (dbg_lane != nullptr && valid) store_u16<CPL>(dbg_lane + (size_t)x * Dp, Sm);
+    // keys (S << 8 | d); padding keys have 0xff in the top byte
+    uint32_t key[CPL];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      key[2 * i] = prmt(Sm[i], kb[i], 0x6104);
+      key[2 * i + 1] = prmt(Sm[i], kb[i], 0x7325);
+    }
+    uint32_t best = key[0];
+#pragma unroll
+    for (int j = 1; j < CPL; ++j) best = min(best, key[j]);
+    best = group_reduce_min(best, grp);
+    if (lig == 0 && valid) dstar[g.row + x] = (int16_t)(best & 0xffu);
+    if (dsub != nullptr) {
+      // parabola through S(d*-1), S(d*), S(d*+1); the lanes holding the two
+      // neighbours contribute them, every other lane the neutral 0xffffffff
+      const int ds = (int)(best & 0xffu);
+      uint32_t sm = 0xffffffffu, sp = 0xffffffffu;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int d = lig * CPL + j;
+        sm = d + 1 == ds ? key[j] >> 8 : sm;
+        sp = d == ds + 1 ? key[j] >> 8 : sp;
+      }
+      sm = group_reduce_min(sm, grp);
+      sp = group_reduce_min(sp, grp);
+      if (lig == 0 && valid) {
+        int v = 16 * ds;
+        if (ds > 0 && ds < g.D - 1) {
+          // d* is the smallest argmin: den = S(d*-1) - 2 S(d*) + S(d*+1) > 0 and
+          // 16 (S(d*-1) - S(d*+1)) > -16 den, so the biased numerator is positive:
+          // offset = floor((16 (sm - sp) + den) / (2 den)) = that quotient - 8
+          const uint32_t s0 = best >> 8, den = sm + sp - 2u * s0;
+          v += (int)((16u * sm + 17u * den - 16u * sp) / (2u * den)) - 8;
+        }
+        dsub[g.row + x] = (int16_t)v;
+      }
+    }
+    // right view: group 0 (x rising) moves keys up a slot per step, group 1
+    // (x falling) down a slot; both fold in S(x, d)
+    // (shuffles run on every lane: the full-warp mask requires it)
+    const uint32_t sh_up = __shfl_up_sync(kFull, w.acc[CPL - 1], 1, 16);
+    const uint32_t sh_dn = __shfl_down_sync(kFull, w.acc[0], 1, 16);
+    const uint32_t in_up = lig == 0 ? 0xffffffffu : sh_up;
+    const uint32_t in_dn = lig == 15 ? 0xffffffffu : sh_dn;
+    if (valid) {
+      uint32_t nacc[CPL];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const uint32_t lower = j == 0 ? in_up : w.acc[j - 1];
+        const uint32_t upper = j == CPL - 1 ? in_dn : w.acc[j + 1];
+        nacc[j] = min(g.fwd ? lower : upper, key[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) w.acc[j] = nacc[j];
+      const int elane = g.fwd ? g.lastLig : 0;
+      const int xr = g.fwd ? x - (g.D - 1) : x;
+      if (lig == elane && xr >= 0) {
+        uint32_t v = w.acc[0];
+        if (g.fwd) {
+          if (FULLD) {
+            v = w.acc[CPL - 1];
+          } else {
+#pragma unroll
+            for (int j = 1; j < CPL; ++j)
+              if (j == g.lastSlot) v = w.acc[j];
+          }
+        }
+        const bool fin = g.fwd ? xr >= g.xm : x + g.D - 1 < g.xm;
+        if (fin)
+          dprime[g.row + xr] = (int16_t)(v & 0xffu);
+        else
+          atomicMin(&merge[xr - g.mbase], v);
+      }
+    }
+  }
+}
+
+template <int CPL, bool S8, int NP, bool FULLD>
+__global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs a) {
+  using CF = RowCfg<CPL, S8>;
+  constexpr int K = CF::K, S = CF::S, Dp = CF::Dp, SB = CF::SB;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * CF::kStage);
+  uint32_t *merge = reinterpret_cast<uint32_t *>(smem + S * CF::kStage + S * 8);
+  const int lane = threadIdx.x & 31, grp = lane >> 4, lig = lane & 15;
+  const int y = blockIdx.x, f = blockIdx.y;
+  RowGeom g;
+  g.W = a.k.W;
+  g.D = a.k.D;
+  g.fwd = grp == 0;
+  g.xm = g.W / 2;
+  g.delay = g.W & 1;                       // group 0 idles in step 0 when W is odd
+  g.mbase = g.xm - g.D + 1;                // merge slot i holds right pixel mbase + i
+  g.lastLig = (g.D - 1) / CPL;
+  g.lastSlot = (g.D - 1) % CPL;
+  g.row = (size_t)y * g.W;
+  const int W = g.W, D = g.D;
+  const size_t fcells = frame_cells(a.k), fpx = frame_px(a.k);
+  const uint8_t *cost = a.cost + f * fcells;
+  const uint16_t *part0 = a.part[0] + f * fcells, *part1 = a.part[1] + f * fcells, *part2 = a.part[2] + f * fcells;
+  int16_t *dstar = a.dstar + f * fpx, *dprime = a.dprime + f * fpx;
+  int16_t *dsub = a.dsub != nullptr ? a.dsub + f * fpx : nullptr;
+  uint16_t *dbg_lane = (f == 0 && a.dbg_sum != nullptr) ? a.dbg_sum + g.row * Dp + lig * CPL : nullptr;
+  // the row spill region of this frame
+  uint8_t *spill = static_cast<uint8_t *>(a.spill) + f * 4 * fcells * 2 + 3 * fcells * SB;
+  uint8_t *spill_lane = spill + (g.row * Dp + lig * CPL) * SB;
+  const int tmid = g.xm + g.delay;         // both first halves end here
+  const int T = W + g.delay;               // lockstep steps
+  const int c1 = (tmid + K - 1) / K, c2 = (T - tmid + K - 1) / K, nch = c1 + c2;
+  for (int i = lane; i < kMaxDisp; i += 32) merge[i] = 0xffffffffu;
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  uint32_t z[CPL / 4];
+  pad_bytes<CPL>(D, lig, z);
+  const uint32_t edge_lo = lig == 0 ? 0xffffffffu : 0u, edge_hi = lig == 15 ? 0xffffffffu : 0u;
+  const StepConsts sc = a.sc;
+  uint32_t kb[CPL / 2];
+#pragma unroll
+  for (int i = 0; i < CPL / 2; ++i) {
+    const int d0 = lig * CPL + 2 * i;
+    kb[i] = (uint32_t)(d0 & 0xff) | ((uint32_t)((d0 + 1) & 0xff) << 8) | (d0 >= D ? 0xff0000u : 0u) |
+            (d0 + 1 >= D ? 0xff000000u : 0u);
+  }
+  auto chunk = [&](int c, int &t_lo, int &t_hi) {
+    if (c < c1) {
+      t_lo = c * K;
+      t_hi = min(tmid, t_lo + K);
+    } else {
+      t_lo = tmid + (c - c1) * K;
+      t_hi = min(T, t_lo + K);
+    }
+  };
+  // pixels of group gg in steps [t_lo, t_hi): [x_lo, x_lo + n)
+  auto span = [&](int gg, int t_lo, int t_hi, int &x_lo, int &n) {
+    int a0 = gg == 0 ? t_lo - g.delay : W - t_hi;
+    int a1 = gg == 0 ? t_hi - 1 - g.delay : W - 1 - t_lo;
+    a0 = max(a0, 0);
+    a1 = min(a1, W - 1);
+    x_lo = a0;
+    n = a1 >= a0 ? a1 - a0 + 1 : 0;
+  };
+  auto issue = [&](int c) {
+    int t_lo, t_hi;
+    chunk(c, t_lo, t_hi);
+    const bool second = c >= c1;
+    const int stage = c % S;
+    int xl0, nn0, xl1, nn1;
+    span(0, t_lo, t_hi, xl0, nn0);
+    span(1, t_lo, t_hi, xl1, nn1);
+    const uint32_t per_px = (uint32_t)(Dp * (second ? 1 + SB + 2 * NP : 1));
+    if (lane == 0) mbar_expect_tx(&bars[stage], (uint32_t)(nn0 + nn1) * per_px);
+    __syncwarp();
+    // lanes 0..4 serve group 0, lanes 16..20 group 1: cost, other group's spill, parts
+    const int xl = grp ? xl1 : xl0, nn = grp ? nn1 : nn0, j = lig;
+    if (nn > 0) {
+      uint8_t *st = smem + stage * CF::kStage + grp * CF::kGroup;
+      const size_t cell = (g.row + xl) * Dp;
+      if (j == 0) bulk_g2s(st, cost + cell, (uint32_t)(nn * Dp), &bars[stage]);
+      if (second) {
+        if (j == 1) bulk_g2s(st + CF::kCost, spill + cell * SB, (uint32_t)(nn * Dp * SB), &bars[stage]);
+        if (j >= 2 && j < 2 + NP)
+          bulk_g2s(st + CF::kCost + CF::kSpill + (j - 2) * CF::kPart,
+                   (j == 2 ? part0 : (j == 3 ? part1 : part2)) + cell, (uint32_t)(nn * Dp * 2), &bars[stage]);
+      }
+    }
+  };
+  RowWalk<CPL> w;
+#pragma unroll
+  for (int i = 0; i < CPL / 2; ++i) w.L[i] = 0;
+  w.mm = 0;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) w.acc[j] = 0xffffffffu;
+  bool ok = true;
+  int issued = 0;
+  for (int c = 0; c < nch; ++c) {
+    // second-half fills read the other group's spill: issue them only after
+    // both first halves are stored and fenced (end of chunk c1 - 1)
+    while (issued < nch && issued < c + S && (issued < c1 || c >= c1)) issue(issued++);
+    if (!ring_wait<S>(bars, c, issued, a.err)) {
+      ok = false;
+      break;
+    }
+    int t_lo, t_hi;
+    chunk(c, t_lo, t_hi);
+    int xl, nn;
+    span(grp, t_lo, t_hi, xl, nn);
+    const uint8_t *stg = smem + (c % S) * CF::kStage + grp * CF::kGroup;
+    // a walk starts at step delay (group 0) or 0 (group 1)
+    const bool restart = t_lo <= g.delay && 0 < t_hi;
+#define ROW_CHUNK(SEC, RS)                                                                                   \
+  row_chunk<CPL, S8, NP, FULLD, SEC, RS>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp, lig,   \
+                                         spill_lane, dstar, dprime, dsub, dbg_lane, merge)
+    if (c < c1) {
+      if (restart) ROW_CHUNK(false, true); else ROW_CHUNK(false, false);
+    } else {
+      if (restart) ROW_CHUNK(true, true); else ROW_CHUNK(true, false);
+    }
+#undef ROW_CHUNK
+    __syncwarp();
+    if (c + 1 == c1) {
+      // both groups' first halves are stored: make them visible to the bulk copies
+      fence_proxy_async_global();
+      __syncwarp();
+    }
+  }
+  if (ok && g.fwd) {
+    // right pixels x' = W-1-d whose diagonal leaves the image: slot d of group 0
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int d = lig * CPL + j, xr = W - 1 - d;
+      if (d < D - 1 && xr >= 0) {
+        if (xr >= g.xm)
+          dprime[g.row + xr] = (int16_t)(w.acc[j] & 0xffu);
+        else
+          atomicMin(&merge[xr - g.mbase], w.acc[j]);
+      }
+    }
+  }
+  __syncwarp();
+  if (ok) {
+    // right pixels whose diagonal crosses xm: both groups contributed
+    for (int i = lane; i < D - 1; i += 32) {
+      const int xr = g.mbase + i;
+      if (xr >= 0 && xr < g.xm) dprime[g.row + xr] = (int16_t)(merge[i] & 0xffu);
+    }
+  }
+}
+
+// opt in once per device to the kernel's dynamic shared memory
+template <typename Kern>
+static cudaError_t smem_optin(Kern kern, int bytes, bool (&done)[64]) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+template <int CPL, bool S8, int FAM, int NWARP>
+static cudaError_t launch_line_family_w(const LineArgs &a, int nf, cudaStream_t s) {
+  using CF = LineCfg<CPL, S8, NWARP>;
+  static bool done[64] = {};
+  cudaError_t e = smem_optin(k_agg_lines<CPL, S8, FAM, NWARP>, CF::kSmem, done);
+  if (e != cudaSuccess) return e;
+  const int lines_per_cta = 2 * CF::kWarps;
+  dim3 grid((a.k.W + lines_per_cta - 1) / lines_per_cta, nf);
+  k_agg_lines<CPL, S8, FAM, NWARP><<<grid, 32 * CF::kWarps, CF::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// warps per CTA from the context's tuning (2, 4 or 8)
+template <int CPL, bool S8, int FAM>
+static cudaError_t launch_line_family(const LineArgs &a, int nf, cudaStream_t s) {
+  switch (a.k.line_warps) {
+    case 2: return launch_line_family_w<CPL, S8, FAM, 2>(a, nf, s);
+    case 8: return launch_line_family_w<CPL, S8, FAM, 8>(a, nf, s);
+    default: return launch_line_family_w<CPL, S8, FAM, 4>(a, nf, s);
+  }
+}
+
+template <int CPL, bool S8>
+cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  LineArgs a;
+  a.k = k;
+  a.cost = b.cost;
+  for (int i = 0; i < 3; ++i) a.part[i] = b.part[i];
+  a.spill = b.spill;
+  a.err = b.err;
+  a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
+  a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
+  // the three families are independent: one launch each, back to back
+  cudaError_t e = launch_line_family<CPL, S8, 0>(a, nf, s);
+  if (e != cudaSuccess || k.num_paths != 8) return e;
+  e = launch_line_family<CPL, S8, 1>(a, nf, s);
+  if (e != cudaSuccess) return e;
+  return launch_line_family<CPL, S8, 2>(a, nf, s);
+}
+
+template <int CPL, bool S8, int NP, bool FULLD>
+static cudaError_t launch_rows_v(const RowArgs &a, int nf, cudaStream_t s) {
+  using CF = RowCfg<CPL, S8>;
+  static bool done[64] = {};
+  cudaError_t e = smem_optin(k_agg_rows<CPL, S8, NP, FULLD>, CF::kSmem, done);
+  if (e != cudaSuccess) return e;
+  k_agg_rows<CPL, S8, NP, FULLD><<<dim3(a.k.H, nf), 32, CF::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CPL, bool S8>
+cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  RowArgs a;
+  a.k = k;
+  a.cost = b.cost;
+  for (int i = 0; i < 3; ++i) a.part[i] = b.part[i];
+  a.spill = b.spill;
+  a.dstar = b.dstar;
+  a.dprime = b.dprime;
+  a.dsub = k.subpixel ? b.dsub : nullptr;
+  a.dbg_sum = b.dbg_sum;
+  a.err = b.err;
+  a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
+  a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
+  const bool fulld = k.D == k.Dp;
+  if (k.num_paths == 8)
+    return fulld ? launch_rows_v<CPL, S8, 3, true>(a, nf, s) : launch_rows_v<CPL, S8, 3, false>(a, nf, s);
+  return fulld ? launch_rows_v<CPL, S8, 1, true>(a, nf, s) : launch_rows_v<CPL, S8, 1, false>(a, nf, s);
+}
+
+}  // namespace sgmf
+
+// explicit instantiations of one lane width (CPL cells per lane)
+#define SGMF_AGG_INSTANTIATE(CPL)                                                                        \
+  namespace sgmf {                                                                                      \
+  template cudaError_t launch_lines_t<CPL, false>(const KParams &, const Buffers &, int, cudaStream_t); \
+  template cudaError_t launch_lines_t<CPL, true>(const KParams &, const Buffers &, int, cudaStream_t);  \
+  template cudaError_t launch_rows_t<CPL, false>(const KParams &, const Buffers &, int, cudaStream_t);  \
+  template cudaError_t launch_rows_t<CPL, true>(const KParams &, const Buffers &, int, cudaStream_t);   \
+  }

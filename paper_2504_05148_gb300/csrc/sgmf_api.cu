@@ -81,6 +81,7 @@ extern "C" void sgmf_default_params(sgmf_params *p) {
   p->semidense = 1;
   p->consistency = SGMF_CHECK_STEREO_LIDAR;
   p->num_paths = 8;
+  p->subpixel = 0;
 }
 
 extern "C" const char *sgmf_status_string(sgmf_status s) {
@@ -129,6 +130,7 @@ sgmf_status sgmf::validate_params(const sgmf_params &p, std::string &why) {
   if (p.semidense != 0 && p.semidense != 1) return bad("semidense must be 0 or 1");
   if (p.consistency < 0 || p.consistency > 3) return bad("unknown consistency mode");
   if (p.num_paths != 4 && p.num_paths != 8) return bad("num_paths must be 4 or 8");
+  if (p.subpixel != 0 && p.subpixel != 1) return bad("subpixel must be 0 or 1");
   const long mc = max_cost(p);
   if (mc > 255) {
     snprintf(buf, sizeof buf, "largest joint cost %ld exceeds 255 (uint8 cost volume)", mc);
@@ -156,12 +158,13 @@ static void apply_params(sgmf_ctx *c, const sgmf_params &p) {
   k.semidense = p.semidense;
   k.consistency = p.consistency;
   k.num_paths = p.num_paths;
+  k.subpixel = p.subpixel;
   k.nbits = census_bits(p.census);
   c->spill8 = max_cost(p) + p.p2 <= 255;
 }
 
 static void free_all(sgmf_ctx *c) {
-  void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.censL,
+  void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.dsub, c->b.censL,
                   c->b.censR, c->b.pres, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
                   c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.err, c->st_left,
                   c->st_right, c->st_lidar, c->st_out};
@@ -203,6 +206,8 @@ extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, 
   k.Dp = 32 * k.DPL;
   k.MW = k.Dp / 32;
   k.pitch = (width + 15) / 16 * 16;
+  k.line_warps = 4;
+  k.cost_px = 128;
   sgmf_params def;
   sgmf_default_params(&def);
   apply_params(c, def);
@@ -218,6 +223,7 @@ extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, 
   A(dalloc(c, &c->b.dhat, n * 2));
   A(dalloc(c, &c->b.dstar, n * 2));
   A(dalloc(c, &c->b.dprime, n * 2));
+  A(dalloc(c, &c->b.dsub, n * 2));
   A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censL), n * 8));
   A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censR), n * 8));
   A(dalloc(c, &c->b.pres, n * 4 * k.MW));
@@ -426,13 +432,16 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
   const size_t n = (size_t)k.W * k.H;
   size_t need = 0;
   switch (stage) {
-    case SGMF_STAGE_DBAR: case SGMF_STAGE_DHAT: case SGMF_STAGE_DSTAR: case SGMF_STAGE_DPRIME: need = n * 2; break;
+    case SGMF_STAGE_DBAR: case SGMF_STAGE_DHAT: case SGMF_STAGE_DSTAR: case SGMF_STAGE_DPRIME:
+    case SGMF_STAGE_DSUB: need = n * 2; break;
     case SGMF_STAGE_CENSUS_L: case SGMF_STAGE_CENSUS_R: need = n * 8; break;
     case SGMF_STAGE_COST: need = n * k.D; break;
     case SGMF_STAGE_SUM: need = n * k.D * 2; break;
     default: return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: unknown stage %d", stage);
   }
   if (bytes < need) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: need %zu bytes, got %zu", need, bytes);
+  if (stage == SGMF_STAGE_DSUB && !k.subpixel)
+    return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: DSUB needs subpixel = 1");
   if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: SUM needs sgmf_set_debug(c, 1) before sgmf_compute");
   sgmf_status st = sgmf_sync(c);
@@ -444,6 +453,7 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
       break;
     case SGMF_STAGE_DSTAR: CUDA_TRY(c, cudaMemcpy(dst, c->b.dstar, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_DPRIME: CUDA_TRY(c, cudaMemcpy(dst, c->b.dprime, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_DSUB: CUDA_TRY(c, cudaMemcpy(dst, c->b.dsub, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_CENSUS_L:
     case SGMF_STAGE_CENSUS_R: {
       const void *src = stage == SGMF_STAGE_CENSUS_L ? c->b.censL : c->b.censR;

@@ -12,7 +12,9 @@ namespace sgmf {
 //   K_p (clipped), has |d*_p - d-bar_q| <= tc -- i.e. the box-ORed presence
 //   mask has a bit in [d* - tc, d* + tc];
 // otherwise -1.  The raw map d-bar is used, never d-hat.  `consistency`
-// selects the Table V variants.
+// selects the Table V variants.  With the sub-pixel fit on, a kept pixel
+// carries its sub-pixel disparity (1/16 px) instead of d*; the test itself
+// is always on the integer d*.
 __global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b0, int16_t *__restrict__ out) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -43,7 +45,8 @@ __global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b0, int1
     case 3: ok = true; break;
     default: ok = stereo_ok || lidar_ok; break;
   }
-  out[p] = ok ? (int16_t)ds : (int16_t)-1;
+  const int16_t v = k.subpixel ? b.dsub[p] : (int16_t)ds;
+  out[p] = ok ? v : (int16_t)-1;
 }
 
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s) {

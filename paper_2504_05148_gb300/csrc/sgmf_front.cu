@@ -330,46 +330,54 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 // for DSGM) is invalid C-bar = H; otherwise
 //   C-bar = floor(((b-a) H + a q + floor(b/2)) / b),  q = 0 / q1 / q2 for
 // |d - prior| = 0 / 1 / > 1, looked up in a table built on the host.
-// A CTA handles 32 pixels of one row: their right-census window is staged in
-// shared memory, the lanes of a warp walk the disparities of one pixel, and
-// the CTA's [32][Dp] cost rows, assembled in shared memory, leave as 16-byte
-// stores (cells d >= D hold 0).
+// A CTA handles PX pixels of one row (32, 64 or 128, a tuning choice): their
+// right-census window is staged in shared memory, the lanes of a warp walk
+// the disparities of one pixel, and the CTA's [PX][Dp] cost rows, assembled
+// in shared memory, leave as 16-byte stores (cells d >= D hold 0).
 struct CostTable {
-  uint8_t v[3][64];   // [q class][H]
+  uint8_t v[4][64];   // [q class][H]; class 3 (no prior) is the identity
 };
 
-constexpr int kCostPx = 32;
 
-template <typename CT, int DPL>
+template <typename CT>
+__device__ __forceinline__ int hamming(CT a, CT b) {
+  if constexpr (sizeof(CT) == 4)
+    return __popc(a ^ b);
+  else
+    return __popcll(a ^ b);
+}
+
+template <typename CT, int DPL, int PX>
 __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
   constexpr int Dp = 32 * DPL;
-  __shared__ CT cr_s[kCostPx + Dp];
-  __shared__ CT cl_s[kCostPx];
-  __shared__ int pd_s[kCostPx];
-  __shared__ uint8_t tab_s[3 * 64];
-  __shared__ __align__(16) uint8_t out_s[kCostPx * Dp];   // the block's cost rows, [x][d]
+  __shared__ CT cr_s[PX + Dp];
+  __shared__ CT cl_s[PX];
+  __shared__ int pd_s[PX];
+  __shared__ uint8_t tab_s[4 * 64];
+  __shared__ __align__(16) uint8_t out_s[PX * Dp];   // the block's cost rows, [x][d]
   const Buffers b = frame_view(k, b0, blockIdx.z);
-  const int x0 = blockIdx.x * kCostPx, y = blockIdx.y, W = k.W;
+  const int x0 = blockIdx.x * PX, y = blockIdx.y, W = k.W;
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
   const int base = x0 - (Dp - 1);               // cr_s[i] = cR(base + i)
-  for (int i = threadIdx.x; i < kCostPx + Dp - 1; i += blockDim.x) {
+  for (int i = threadIdx.x; i < PX + Dp - 1; i += blockDim.x) {
     const int xx = base + i;
     cr_s[i] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
   }
-  if (threadIdx.x < kCostPx) {
+  if (threadIdx.x < PX) {
     const int xx = x0 + threadIdx.x;
+    const int pd = xx < W ? prior[xx] : -1;
     cl_s[threadIdx.x] = xx < W ? cl[xx] : (CT)0;
-    pd_s[threadIdx.x] = xx < W ? prior[xx] : -1;
+    pd_s[threadIdx.x] = pd;
   }
-  for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
+  for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
   // lanes walk disparities (d = lane + 32 j): the right-census reads of a warp
   // are consecutive words, free of bank conflicts
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int npx = min(kCostPx, W - x0);
+  const int npx = min(PX, W - x0);
   for (int px = warp; px < npx; px += 8) {
     const int x = x0 + px;
     const CT c = cl_s[px];
@@ -377,17 +385,9 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
       const int d = lane + 32 * j;
-      uint32_t v = 0;
-      if (d < k.D) {
-        const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr_s[px - d + Dp - 1])) : k.nbits;
-        if (pd < 0) {
-          v = (uint32_t)h;
-        } else {
-          const int ad = abs(d - pd);
-          v = tab_s[(ad == 0 ? 0 : (ad == 1 ? 64 : 128)) + h];
-        }
-      }
-      out_s[px * Dp + d] = (uint8_t)v;
+      const int h = (x >= d) ? hamming<CT>(c, cr_s[px - d + Dp - 1]) : k.nbits;
+      const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
+      out_s[px * Dp + d] = d < k.D ? tab_s[cls * 64 + h] : (uint8_t)0;
     }
   }
   __syncthreads();
@@ -398,14 +398,24 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
 }
 
+template <typename CT, int PX>
+static void launch_cost_px(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
+  dim3 grid((k.W + PX - 1) / PX, k.H, nf);
+  switch (k.DPL) {
+    case 2: k_cost<CT, 2, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
+    case 4: k_cost<CT, 4, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
+    case 6: k_cost<CT, 6, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
+    default: k_cost<CT, 8, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
+  }
+}
+
+// pixels per CTA from the context's tuning (32, 64 or 128)
 template <typename CT>
 static void launch_cost_t(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
-  dim3 grid((k.W + kCostPx - 1) / kCostPx, k.H, nf);
-  switch (k.DPL) {
-    case 2: k_cost<CT, 2><<<grid, 256, 0, s>>>(k, b, tab); break;
-    case 4: k_cost<CT, 4><<<grid, 256, 0, s>>>(k, b, tab); break;
-    case 6: k_cost<CT, 6><<<grid, 256, 0, s>>>(k, b, tab); break;
-    default: k_cost<CT, 8><<<grid, 256, 0, s>>>(k, b, tab); break;
+  switch (k.cost_px) {
+    case 32: launch_cost_px<CT, 32>(k, b, nf, tab, s); break;
+    case 64: launch_cost_px<CT, 64>(k, b, nf, tab, s); break;
+    default: launch_cost_px<CT, 128>(k, b, nf, tab, s); break;
   }
 }
 
@@ -417,6 +427,7 @@ cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t
       const long v = ((long)(k.b - k.a) * h + (long)k.a * qs[c] + k.b / 2) / k.b;
       tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
     }
+  for (int h = 0; h < 64; ++h) tab.v[3][h] = (uint8_t)h;
   if (k.census == 1)
     launch_cost_t<uint64_t>(k, b, nf, tab, s);
   else

@@ -34,13 +34,15 @@ struct KParams {
   int pitch;                  // image pitch in bytes
   int p1, p2, q1, q2, a, b;   // alpha = a / b
   int ts, rs, tc, rc, lr;
-  int census, semidense, consistency, num_paths;
-  int nbits;                  // census bits (31 or 62)
+  int census, semidense, consistency, num_paths, subpixel;
+  int nbits;
+  int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA                  // census bits (31 or 62)
 };
 
 struct Buffers {   // base pointers of frame 0
   uint8_t *imgL, *imgR;       // pitched copies
   int16_t *dbar, *dhat, *dstar, *dprime;
+  int16_t *dsub;              // sub-pixel disparity (1/16 px)
   void *censL, *censR;        // u32 or u64 per pixel
   uint32_t *pres, *boxS, *boxC, *boxTmp;   // [MW][H][W]
   uint8_t *cost;              // [H][W][Dp]
@@ -65,6 +67,7 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
   v.dhat = b.dhat + f * px;
   v.dstar = b.dstar + f * px;
   v.dprime = b.dprime + f * px;
+  v.dsub = b.dsub + f * px;
   const size_t cw = k.census == 1 ? 8 : 4;
   v.censL = static_cast<uint8_t *>(b.censL) + f * px * cw;
   v.censR = static_cast<uint8_t *>(b.censR) + f * px * cw;

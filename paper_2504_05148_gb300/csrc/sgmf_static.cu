@@ -89,6 +89,8 @@ extern "C" sgmf_status sgmf_check_static(int width, int height, int max_disp, co
     return fail_static(SGMF_ERR_SHAPE, "sgmf_check_static: need 1 <= width, height <= 8192, 1 <= max_disp <= 256");
   std::string why;
   if (validate_params(*p, why) != SGMF_OK) return fail_static(SGMF_ERR_PARAM, "sgmf_check_static: " + why);
+  if (p->subpixel != 0)
+    return fail_static(SGMF_ERR_PARAM, "sgmf_check_static: subpixel must be 0 (integer output only)");
   KParams k{};
   k.W = width;
   k.H = height;

@@ -21,7 +21,7 @@ SGMF_OK, SGMF_ERR_ARG, SGMF_ERR_PARAM, SGMF_ERR_SHAPE, SGMF_ERR_OOM, SGMF_ERR_CU
 SGMF_CENSUS_CS9X7, SGMF_CENSUS_9X7 = 0, 1
 SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 0, 1, 2, 3
 (SGMF_STAGE_DBAR, SGMF_STAGE_CENSUS_L, SGMF_STAGE_CENSUS_R, SGMF_STAGE_DHAT, SGMF_STAGE_COST,
- SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME) = range(8)
+ SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME, SGMF_STAGE_DSUB) = range(9)
 
 # symbols declared in include/sgmf.h
 EXPORTS = (
@@ -42,7 +42,7 @@ class SgmfError(RuntimeError):
 class sgmf_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "p1", "p2", "q1", "q2", "alpha_num", "alpha_den", "ts", "rs", "tc", "rc",
-        "lr_max_diff", "census", "semidense", "consistency", "num_paths")]
+        "lr_max_diff", "census", "semidense", "consistency", "num_paths", "subpixel")]
 
 
 @dataclass
@@ -64,6 +64,7 @@ class Params:
     semidense: int = 1
     consistency: int = SGMF_CHECK_STEREO_LIDAR
     num_paths: int = 8
+    subpixel: int = 0
 
     def to_c(self) -> sgmf_params:
         return sgmf_params(**asdict(self))
@@ -313,6 +314,7 @@ class Context:
         spec = {
             SGMF_STAGE_DBAR: (np.int16, shape2), SGMF_STAGE_DHAT: (np.int16, shape2),
             SGMF_STAGE_DSTAR: (np.int16, shape2), SGMF_STAGE_DPRIME: (np.int16, shape2),
+            SGMF_STAGE_DSUB: (np.int16, shape2),
             SGMF_STAGE_CENSUS_L: (np.uint64, shape2), SGMF_STAGE_CENSUS_R: (np.uint64, shape2),
             SGMF_STAGE_COST: (np.uint8, shape2 + (self.D,)), SGMF_STAGE_SUM: (np.uint16, shape2 + (self.D,)),
         }[stage]

@@ -49,6 +49,23 @@ def test_default_params_are_table_ii(libpath):
     assert (p.alpha_num, p.alpha_den) == (7, 10)
     assert (p.ts, p.rs, p.tc, p.rc) == (2, 6, 2, 20)
     assert p.num_paths == 8 and p.semidense == 1 and p.lr_max_diff == 1
+    assert p.subpixel == 0
+
+
+def test_params_struct_matches_header_field_order():
+    """The ctypes mirror lists the header's sgmf_params fields in order (all int32)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "sgmf.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} sgmf_params;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        assert decl.startswith("int32_t "), decl
+        names += [n.strip() for n in decl[len("int32_t "):].split(",")]
+    assert [f[0] for f in sgmf.sgmf_params._fields_] == names
 
 
 def test_status_strings(libpath):
