@@ -1,6 +1,7 @@
 """Throughput benchmark of the stereo-LiDAR SGM pipeline (one JSON line).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+    python bench.py --workload mixed [--steps K] [--warmup W]
 
 Workload: 1242 x 375 stereo pairs with D = 128 and 64-beam LiDAR (about 5 %
 density), the KITTI-shaped synthetic scene of paper_2504_05148_gb300.scenes;
@@ -11,6 +12,11 @@ are resident in HBM before the timed region; L2 is flushed (512 MiB write)
 between steps, outside the timed events.  Under torchrun every rank runs
 its own frames (weak scaling, no collective on the data path); the step time
 is the max over ranks.
+
+--workload mixed: 48 pairs, 12 each of 640x480 D=64, 1242x375 D=128,
+1280x720 D=192 and 1920x1080 D=256, run as one CUDA-graph launch per step
+(classes of equal shape batched, classes as parallel graph branches) after
+the autotuner has picked each class's launch tuning.
 """
 from __future__ import annotations
 
@@ -177,6 +183,111 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_mixed(args, rank, world):
+    """The mixed-size batch as one graph launch per step (weak scaling per rank)."""
+    import numpy as np
+    import torch
+    from paper_2504_05148_gb300 import build as _build
+    from paper_2504_05148_gb300 import scenes
+    _build.build()
+    from paper_2504_05148_gb300 import sgmf
+
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scs = scenes.mixed_batch(12, distinct=args.mixed_distinct, base_seed=4000 + 1000 * rank)
+    shapes = [(s.W, s.H, s.D) for s in scs]
+    whd = sum(w * h * d for w, h, d in shapes)
+    m = sgmf.Multi(shapes)
+    views = [m.frame_views(i) for i in range(len(scs))]
+    for v, s in zip(views, scs):
+        v[0].copy_(torch.from_numpy(s.left))
+        v[1].copy_(torch.from_numpy(s.right))
+        v[2].copy_(torch.from_numpy(s.lidar))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    if not args.no_tune:
+        m.autotune(reps=2)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        m.launch(stream)
+    m.sync()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a.record(stream)
+            m.launch(stream)
+            b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    clk = clocks.stop()
+    m.sync()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = args.steps * whd * world / (total_ms * 1e-3)
+    # end to end: every step copies the 48 pairs in from pinned host memory and
+    # the 48 outputs back, around the same graph launch
+    hin = [(torch.from_numpy(s.left).pin_memory(), torch.from_numpy(s.right).pin_memory(),
+            torch.from_numpy(s.lidar).pin_memory()) for s in scs]
+    hout = [torch.empty((s.H, s.W), dtype=torch.int16).pin_memory() for s in scs]
+    bi = sum(s.W * s.H * 6 for s in scs)
+    bo = sum(s.W * s.H * 2 for s in scs)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for v, h in zip(views, hin):
+                v[0].copy_(h[0], non_blocking=True)
+                v[1].copy_(h[1], non_blocking=True)
+                v[2].copy_(h[2], non_blocking=True)
+            m.launch(stream)
+            for v, h in zip(views, hout):
+                h.copy_(v[3], non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(args.warmup):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    dt = time.perf_counter() - t0
+    for v, h in zip(views, hout):
+        if not torch.equal(v[3].cpu(), h):
+            raise RuntimeError("host copy of the output differs from the device buffer")
+    if rank != 0:
+        m.close()
+        return 0
+    classes = [{"shape": list(sh), "frames": n, "line_warps": t[0], "cost_px": t[1]} for sh, n, t in m.classes()]
+    line = {
+        "metric": "W*H*D/s and frames/s, 48 mixed-size pairs per graph launch", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "frames_per_s": args.steps * len(scs) * world / (total_ms * 1e-3),
+        "config": {"workload": "mixed48_640x480d64_1242x375d128_1280x720d192_1920x1080d256",
+                   "pairs_per_step": len(scs), "distinct_pairs_per_shape": args.mixed_distinct,
+                   "graph_launches_per_step": 1, "classes": classes, "autotune_s": round(tune_s, 2),
+                   "l2": "flushed by a 512 MiB write between steps", "parallelism": f"replicas x{world}"},
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": args.steps * whd / dt, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "frames_per_s": args.steps * len(scs) / dt},
+        "gpu_launches": args.steps * m.launches(), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,11 +297,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed"])
+    ap.add_argument("--mixed-distinct", type=int, default=3,
+                    help="distinct generated pairs per shape in the mixed batch (reused cyclically)")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "mixed":
+        return run_mixed(args, rank, world)
 
     import numpy as np
     import torch
@@ -210,6 +327,12 @@ def main():
     dout = torch.empty((B, H, W), dtype=torch.int16, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
+    tuning = None
+    if not args.no_tune:
+        # launch tuning only (results are bit-identical for every candidate)
+        tuning, _ = sgmf.sgmf_autotune(ctx.handle, B, dl.data_ptr(), dr.data_ptr(), dli.data_ptr(),
+                                       dout.data_ptr(), 2)
+        stream.synchronize()
 
     def step():
         start = torch.cuda.Event(enable_timing=True)
@@ -340,7 +463,8 @@ def main():
         "frames_per_s": frames_total / (total_ms * 1e-3),
         "config": {"workload": WORKLOAD, "W": W, "H": H, "D": D, "frames_per_step": B,
                    "batched_launch": True, "l2": "flushed by a 512 MiB write between steps",
-                   "lidar": "64 beams, ~5% density", "parallelism": f"replicas x{world}"},
+                   "lidar": "64 beams, ~5% density", "parallelism": f"replicas x{world}",
+                   "tuning": None if tuning is None else {"line_warps": tuning[0], "cost_px": tuning[1]}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
         "kernel_ms_avg": {k: round(v, 4) for k, v in sorted(avg.items())},

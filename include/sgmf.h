@@ -204,6 +204,81 @@ sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n
 /* Bytes of device memory the context holds. */
 size_t sgmf_device_bytes(const sgmf_ctx *c);
 
+/* ---- Launch tuning (no counterpart in the paper) -----------------------
+ * Launch shapes only: every choice gives bit-identical results. */
+typedef struct {
+    int32_t line_warps;   /* warps per CTA of the vertical/diagonal line kernels
+                             (each warp walks two lines): 2, 4 (default) or 8 */
+    int32_t cost_px;      /* pixels of one row per CTA of the cost kernel: 32, 64 or
+                             128 (default) */
+} sgmf_tuning;
+
+/* Set / read the context's tuning.  SGMF_ERR_ARG for other values. */
+sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t);
+sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t);
+
+/* Autotuner.  Runs sgmf_compute_batch(c, n, left, right, lidar, out) on the
+ * caller's DEVICE frames once per candidate (all 3 x 3 tunings) as a
+ * warm-up, then `reps` timed runs (CUDA events on the context's stream,
+ * 1 <= reps <= 100); keeps the candidate with the smallest median time in
+ * the context and returns it in *best and its median in *best_ms (either may
+ * be NULL).  Synchronises the stream; out receives the (identical) output. */
+sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right, const float *lidar,
+                          int16_t *out, int reps, sgmf_tuning *best, float *best_ms);
+
+/* ---- Mixed-size batches in one CUDA-graph launch (no counterpart in the paper)
+ * A multi-batch holds n frames whose shapes may differ.  Frames of equal
+ * (width, height, max_disp) form a class; each class owns one batched context
+ * (all of a class's frames go through each kernel in one launch), one stream
+ * and RESIDENT device buffers for its frames' inputs and outputs, so that the
+ * whole batch can be captured once as a CUDA graph (the classes as parallel
+ * branches) and replayed with one cudaGraphLaunch per call.  Errors of these
+ * calls are reported in sgmf_last_error(NULL). */
+typedef struct {
+    int32_t width, height, max_disp;
+} sgmf_shape;
+typedef struct sgmf_multi sgmf_multi;
+
+/* Creates the batch on the current device; p = NULL selects Table II.
+ * Errors: SGMF_ERR_ARG, SGMF_ERR_SHAPE (1 <= n <= 4096, shapes as in
+ * sgmf_create), SGMF_ERR_PARAM, SGMF_ERR_OOM / SGMF_ERR_CUDA. */
+sgmf_status sgmf_multi_create(const sgmf_shape *shapes, int n, const sgmf_params *p, sgmf_multi **out);
+
+/* Device buffers of frame i (any pointer may be NULL): left / right uint8
+ * H x W, lidar float32 H x W (0 = no return; zero-filled at creation), out
+ * int16 H x W.  They stay valid and fixed until sgmf_multi_destroy: fill the
+ * inputs (on any stream, ordered before sgmf_multi_launch) and read out_disp
+ * after it. */
+sgmf_status sgmf_multi_frame(sgmf_multi *m, int i, uint8_t **left, uint8_t **right, float **lidar,
+                             int16_t **out);
+
+/* Number of classes; shape, frame count and tuning of class `cls`. */
+int sgmf_multi_classes(const sgmf_multi *m);
+sgmf_status sgmf_multi_class_info(const sgmf_multi *m, int cls, sgmf_shape *shape, int *frames,
+                                  sgmf_tuning *t);
+
+/* sgmf_autotune for every class on its resident frames (`reps` timed runs
+ * per candidate); drops a captured graph so that the next launch recaptures
+ * with the chosen tunings.  Synchronous. */
+sgmf_status sgmf_multi_autotune(sgmf_multi *m, int reps);
+
+/* Runs the whole batch on `stream` (NULL = the batch's own stream) as one
+ * CUDA graph launch.  The first call (and the first after autotuning) runs
+ * every class once outside capture, then captures the batch into a graph;
+ * later calls only launch the graph.  Asynchronous: sgmf_multi_sync waits and
+ * surfaces device errors (including SGMF_ERR_TIMEOUT). */
+sgmf_status sgmf_multi_launch(sgmf_multi *m, void *stream);
+sgmf_status sgmf_multi_sync(sgmf_multi *m);
+
+/* Kernel launches one sgmf_multi_launch replays (summed over classes). */
+int sgmf_multi_launches(const sgmf_multi *m);
+
+/* Device bytes held (contexts and resident buffers). */
+size_t sgmf_multi_device_bytes(const sgmf_multi *m);
+
+/* Frees everything (NULL-safe); waits for the batch's work first. */
+void sgmf_multi_destroy(sgmf_multi *m);
+
 /* The three-view consistency stage alone, without a context and without
  * allocating anything.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory where they call it

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -502,3 +503,83 @@ extern "C" sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float 
 }
 
 extern "C" size_t sgmf_device_bytes(const sgmf_ctx *c) { return c ? c->bytes : 0; }
+
+// ---- launch tuning -------------------------------------------------------------
+static bool valid_tuning(const sgmf_tuning &t) {
+  return (t.line_warps == 2 || t.line_warps == 4 || t.line_warps == 8) &&
+         (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128);
+}
+
+extern "C" sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t) {
+  if (!c || !t) return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: NULL argument");
+  if (!valid_tuning(*t))
+    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: need line_warps in {2,4,8} and cost_px in {32,64,128}");
+  c->k.line_warps = t->line_warps;
+  c->k.cost_px = t->cost_px;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t) {
+  if (!c || !t) return SGMF_ERR_ARG;
+  t->line_warps = c->k.line_warps;
+  t->cost_px = c->k.cost_px;
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                     const float *lidar, int16_t *out, int reps, sgmf_tuning *best,
+                                     float *best_ms) {
+  if (!c) return SGMF_ERR_ARG;
+  if (reps < 1 || reps > 100) return fail(c, SGMF_ERR_ARG, "sgmf_autotune: need 1 <= reps <= 100 (got %d)", reps);
+  const bool prof = c->profiling;
+  c->profiling = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  sgmf_status st = SGMF_OK;
+  sgmf_tuning keep{c->k.line_warps, c->k.cost_px}, win = keep;
+  float win_ms = 0.0f;
+  bool have = false;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = fail(c, SGMF_ERR_CUDA, "sgmf_autotune: cudaEventCreate failed");
+  }
+  const int warps[3] = {2, 4, 8}, pxs[3] = {32, 64, 128};
+  std::vector<float> t;
+  for (int i = 0; i < 9 && st == SGMF_OK; ++i) {
+    c->k.line_warps = warps[i / 3];
+    c->k.cost_px = pxs[i % 3];
+    st = sgmf_compute_batch(c, n, left, right, lidar, out);   // warm-up (and first-use attributes)
+    t.clear();
+    for (int r = 0; r < reps && st == SGMF_OK; ++r) {
+      cudaEventRecord(e0, c->stream);
+      st = sgmf_compute_batch(c, n, left, right, lidar, out);
+      cudaEventRecord(e1, c->stream);
+      if (st != SGMF_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = fail(c, SGMF_ERR_CUDA, "sgmf_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms);
+    }
+    if (st != SGMF_OK) break;
+    st = sgmf_sync(c);
+    if (st != SGMF_OK) break;
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    if (!have || med < win_ms) {
+      have = true;
+      win_ms = med;
+      win = sgmf_tuning{c->k.line_warps, c->k.cost_px};
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->profiling = prof;
+  const sgmf_tuning chosen = st == SGMF_OK ? win : keep;
+  c->k.line_warps = chosen.line_warps;
+  c->k.cost_px = chosen.cost_px;
+  if (st != SGMF_OK) return st;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return SGMF_OK;
+}

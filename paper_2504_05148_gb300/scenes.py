@@ -307,6 +307,39 @@ def indoor(seed: int = 3200) -> Scene:
     return Scene("indoor_640x480_d64", seed, D, left, right, lid, truth)
 
 
+MIXED_SHAPES = ((640, 480, 64), (1242, 375, 128), (1280, 720, 192), (1920, 1080, 256))
+
+
+def mixed(seed: int, W: int, H: int, D: int) -> Scene:
+    """A pair of any size built like the small case (fronto-parallel background
+    and three slanted planes, blurred-noise texture, N(0, 2) sensor noise),
+    with a 64-beam LiDAR model: the frames of the mixed-size batch."""
+    rng = _rng(seed)
+    s = D / 64.0
+    layers = [Layer(a=4.0 * s, bx=0.0, by=0.0, region=np.ones((H, W), bool))]
+    for _ in range(3):
+        w, h = rng.uniform(0.15, 0.45) * W, rng.uniform(0.2, 0.6) * H
+        x0, y0 = rng.uniform(0, W - w), rng.uniform(0, H - h)
+        layers.append(_slanted_rect(rng, H, W, x0, y0, w, h, rng.uniform(10, 54) * s, 4.0 * s,
+                                    min(60.0 * s, D - 1.0), 0.08))
+    base = texture(rng, H, W)
+    fill = texture(rng, H, W)
+    left, right, truth = render(rng, layers, H, W, base, fill, 2.0)
+    lid = _beam_lidar(rng, truth, 64, 1, 0.29, 0.01, D)
+    return Scene(f"mixed_{W}x{H}_d{D}", seed, D, left, right, lid, truth)
+
+
+def mixed_batch(n_per_shape: int = 12, distinct: int = 12, base_seed: int = 4000) -> list[Scene]:
+    """The mixed-size batch: n_per_shape pairs of each of MIXED_SHAPES (48 by
+    default).  `distinct` < n_per_shape reuses that many generated pairs per
+    shape cyclically (generation of the largest pairs takes seconds each)."""
+    out = []
+    for j, (W, H, D) in enumerate(MIXED_SHAPES):
+        made = [mixed(base_seed + 100 * j + i, W, H, D) for i in range(min(distinct, n_per_shape))]
+        out += [made[i % len(made)] for i in range(n_per_shape)]
+    return out
+
+
 def random_small(seed: int, W: int, H: int, D: int, n_planes: int = 2,
                  density: float = 0.08) -> Scene:
     """Small random scene of any shape (edge cases: ragged and tiny sizes)."""

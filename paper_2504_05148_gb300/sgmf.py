@@ -30,6 +30,10 @@ EXPORTS = (
     "sgmf_compute_host_batch", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
     "sgmf_status_string", "sgmf_set_debug", "sgmf_debug_stage", "sgmf_launches_per_compute",
     "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes", "sgmf_check_static",
+    "sgmf_set_tuning", "sgmf_get_tuning", "sgmf_autotune",
+    "sgmf_multi_create", "sgmf_multi_frame", "sgmf_multi_classes", "sgmf_multi_class_info",
+    "sgmf_multi_autotune", "sgmf_multi_launch", "sgmf_multi_sync", "sgmf_multi_launches",
+    "sgmf_multi_device_bytes", "sgmf_multi_destroy",
 )
 
 
@@ -43,6 +47,14 @@ class sgmf_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "p1", "p2", "q1", "q2", "alpha_num", "alpha_den", "ts", "rs", "tc", "rc",
         "lr_max_diff", "census", "semidense", "consistency", "num_paths", "subpixel")]
+
+
+class sgmf_tuning(ctypes.Structure):
+    _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32)]
+
+
+class sgmf_shape(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_disp", ctypes.c_int32)]
 
 
 @dataclass
@@ -114,6 +126,20 @@ def lib(path: str | None = None):
                                   ctypes.POINTER(ctypes.c_int)]),
         "sgmf_device_bytes": (sz, [P]),
         "sgmf_check_static": (i, [i, i, i, prm_p, P, P, P, P, P]),
+        "sgmf_set_tuning": (i, [P, ctypes.POINTER(sgmf_tuning)]),
+        "sgmf_get_tuning": (i, [P, ctypes.POINTER(sgmf_tuning)]),
+        "sgmf_autotune": (i, [P, i, P, P, P, P, i, ctypes.POINTER(sgmf_tuning), ctypes.POINTER(ctypes.c_float)]),
+        "sgmf_multi_create": (i, [ctypes.POINTER(sgmf_shape), i, prm_p, ctx_pp]),
+        "sgmf_multi_frame": (i, [P, i, ctx_pp, ctx_pp, ctx_pp, ctx_pp]),
+        "sgmf_multi_classes": (i, [P]),
+        "sgmf_multi_class_info": (i, [P, i, ctypes.POINTER(sgmf_shape), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(sgmf_tuning)]),
+        "sgmf_multi_autotune": (i, [P, i]),
+        "sgmf_multi_launch": (i, [P, P]),
+        "sgmf_multi_sync": (i, [P]),
+        "sgmf_multi_launches": (i, [P]),
+        "sgmf_multi_device_bytes": (sz, [P]),
+        "sgmf_multi_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -242,6 +268,78 @@ def sgmf_check_static(width: int, height: int, max_disp: int, params: Params, ds
                                    stream or None), None)
 
 
+def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int) -> None:
+    t = sgmf_tuning(line_warps, cost_px)
+    _check(lib().sgmf_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def sgmf_get_tuning(ctx: int) -> tuple[int, int]:
+    t = sgmf_tuning()
+    _check(lib().sgmf_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t.line_warps, t.cost_px
+
+
+def sgmf_autotune(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int,
+                  reps: int = 3) -> tuple[tuple[int, int], float]:
+    """Device pointers; returns ((line_warps, cost_px), median ms) of the winner."""
+    t = sgmf_tuning()
+    ms = ctypes.c_float()
+    _check(lib().sgmf_autotune(ctx, n, left, right, lidar or None, out, reps, ctypes.byref(t),
+                               ctypes.byref(ms)), ctx)
+    return (t.line_warps, t.cost_px), ms.value
+
+
+def sgmf_multi_create(shapes: list[tuple[int, int, int]], params: Params | None = None) -> int:
+    """shapes: (width, height, max_disp) per frame."""
+    arr = (sgmf_shape * len(shapes))(*[sgmf_shape(*s) for s in shapes])
+    out = ctypes.c_void_p()
+    c = params.to_c() if params is not None else None
+    _check(lib().sgmf_multi_create(arr, len(shapes), ctypes.byref(c) if c is not None else None,
+                                   ctypes.byref(out)), None)
+    return out.value
+
+
+def sgmf_multi_frame(m: int, i: int) -> tuple[int, int, int, int]:
+    """Device pointers (left, right, lidar, out) of frame i's resident buffers."""
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    _check(lib().sgmf_multi_frame(m, i, *[ctypes.byref(p) for p in ptrs]), None)
+    return tuple(p.value for p in ptrs)
+
+
+def sgmf_multi_classes(m: int) -> int:
+    return lib().sgmf_multi_classes(m)
+
+
+def sgmf_multi_class_info(m: int, cls: int) -> tuple[tuple[int, int, int], int, tuple[int, int]]:
+    s, n, t = sgmf_shape(), ctypes.c_int(), sgmf_tuning()
+    _check(lib().sgmf_multi_class_info(m, cls, ctypes.byref(s), ctypes.byref(n), ctypes.byref(t)), None)
+    return (s.width, s.height, s.max_disp), n.value, (t.line_warps, t.cost_px)
+
+
+def sgmf_multi_autotune(m: int, reps: int = 3) -> None:
+    _check(lib().sgmf_multi_autotune(m, reps), None)
+
+
+def sgmf_multi_launch(m: int, stream: int | None = None) -> None:
+    _check(lib().sgmf_multi_launch(m, stream or None), None)
+
+
+def sgmf_multi_sync(m: int) -> None:
+    _check(lib().sgmf_multi_sync(m), None)
+
+
+def sgmf_multi_launches(m: int) -> int:
+    return lib().sgmf_multi_launches(m)
+
+
+def sgmf_multi_device_bytes(m: int) -> int:
+    return lib().sgmf_multi_device_bytes(m)
+
+
+def sgmf_multi_destroy(m: int | None) -> None:
+    lib().sgmf_multi_destroy(m)
+
+
 # ---- torch convenience wrapper ------------------------------------------------------
 
 class Context:
@@ -353,3 +451,71 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Multi:
+    """A mixed-size batch replayed as one CUDA graph (resident buffers per frame)."""
+
+    def __init__(self, shapes: list[tuple[int, int, int]], params: Params | None = None):
+        self.shapes = [tuple(s) for s in shapes]
+        self.handle = sgmf_multi_create(self.shapes, params)
+
+    def frame_views(self, i: int):
+        """torch tensors viewing frame i's resident device buffers: left, right, lidar, out."""
+        import torch
+        W, H, _ = self.shapes[i]
+        lp, rp, dp, op = sgmf_multi_frame(self.handle, i)
+        return (_device_view(lp, (H, W), torch.uint8), _device_view(rp, (H, W), torch.uint8),
+                _device_view(dp, (H, W), torch.float32), _device_view(op, (H, W), torch.int16))
+
+    def classes(self):
+        return [sgmf_multi_class_info(self.handle, c) for c in range(sgmf_multi_classes(self.handle))]
+
+    def autotune(self, reps: int = 3) -> None:
+        sgmf_multi_autotune(self.handle, reps)
+
+    def launch(self, stream=None) -> None:
+        sgmf_multi_launch(self.handle, getattr(stream, "cuda_stream", stream))
+
+    def sync(self) -> None:
+        sgmf_multi_sync(self.handle)
+
+    def launches(self) -> int:
+        return sgmf_multi_launches(self.handle)
+
+    def device_bytes(self) -> int:
+        return sgmf_multi_device_bytes(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            sgmf_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _device_view(ptr: int, shape: tuple[int, ...], dtype):
+    """A torch tensor over device memory owned by the library (no copy, no ownership)."""
+    import torch
+
+    class _Mem:
+        def __init__(self, p, nbytes):
+            self.__cuda_array_interface__ = {
+                "shape": shape, "typestr": {torch.uint8: "|u1", torch.float32: "<f4", torch.int16: "<i2"}[dtype],
+                "data": (p, False), "version": 3, "strides": None}
+
+    n = 1
+    for s in shape:
+        n *= s
+    return torch.as_tensor(_Mem(ptr, n), device="cuda")
+
