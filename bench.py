@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
     python bench.py --workload mixed [--steps K] [--warmup W]
+    python bench.py --workload serve [--serve-seconds T]
 
 Workload: 1242 x 375 stereo pairs with D = 128 and 64-beam LiDAR (about 5 %
 density), the KITTI-shaped synthetic scene of paper_2504_05148_gb300.scenes;
@@ -17,6 +18,12 @@ is the max over ranks.
 1280x720 D=192 and 1920x1080 D=256, run as one CUDA-graph launch per step
 (classes of equal shape batched, classes as parallel graph branches) after
 the autotuner has picked each class's launch tuning.
+
+--workload serve: the request loop of the library fed by 6 simulated
+cameras (2 x 1242x375 D=128, 2 x 640x480 D=64, 1280x720 D=192,
+1920x1080 D=256) at 10-30 Hz with Poisson jitter: p50/p99 latency from
+submit (host buffers) to the output in host memory; then the same cameras
+with 4 requests each kept outstanding, for the saturated frames/s.
 """
 from __future__ import annotations
 
@@ -288,6 +295,64 @@ def run_mixed(args, rank, world):
     return 0
 
 
+SERVE_CAMERAS = ((1242, 375, 128, 30.0), (1242, 375, 128, 20.0), (640, 480, 64, 25.0), (640, 480, 64, 15.0),
+                 (1280, 720, 192, 10.0), (1920, 1080, 256, 12.0))
+SERVE_BATCH = 4                 # frames per slot
+SERVE_BUDGET = 128 << 30        # device bytes the request loop may hold (two slots per shape fit)
+
+
+def run_serve(args, rank, world):
+    """Latency under camera-rate load, then saturated throughput (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    from paper_2504_05148_gb300 import build as _build
+    from paper_2504_05148_gb300 import scenes
+    _build.build()
+    from paper_2504_05148_gb300 import serving, sgmf
+    torch.cuda.set_device(0)
+    cams = []
+    for ci, (w, h, d, hz) in enumerate(SERVE_CAMERAS):
+        cams.append(serving.Camera(w, h, d, hz, [scenes.mixed(5000 + 10 * ci + k, w, h, d) for k in range(2)]))
+    kw = {"budget_bytes": SERVE_BUDGET, "max_batch": SERVE_BATCH, "max_slots_per_shape": 2}
+    serving.run(cams, duration_s=1.0, seed=99, **kw)              # warm-up (first-use kernel attributes)
+    clocks = ClockSampler(0)
+    clocks.start()
+    paced = serving.run(cams, duration_s=args.serve_seconds, seed=1, **kw)
+    sat = serving.run_closed(cams, duration_s=max(2.0, args.serve_seconds / 3), depth=4, **kw)
+    clk = clocks.stop()
+    ps, ss = paced.summary(), sat.summary()
+    whd = {ci: c.W * c.H * c.D for ci, c in enumerate(cams)}
+    sat_whd = sum(len(v) * whd[ci] for ci, v in sat.latencies_ms.items()) / sat.wall_s
+    per_cam = [{"shape": [c.W, c.H, c.D], "rate_hz": c.rate_hz, "frames": len(paced.latencies_ms[ci]),
+                "p50_ms": float(np.percentile(paced.latencies_ms[ci], 50)) if paced.latencies_ms[ci] else None,
+                "p99_ms": float(np.percentile(paced.latencies_ms[ci], 99)) if paced.latencies_ms[ci] else None}
+               for ci, c in enumerate(cams)]
+    ok = all(s == sgmf.SGMF_OK for s in paced.statuses + sat.statuses)
+    line = {
+        "metric": "frames/s and p50/p99 latency, 6 simulated cameras through the request loop",
+        "value": ss["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": ss["frames"], "warmup": 1,
+        "ms_per_step": 1e3 / ss["frames_per_s"] if ss["frames_per_s"] else None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "latency_ms": {"p50": ps["p50_ms"], "p99": ps["p99_ms"], "max": ps["max_ms"],
+                       "frames": ps["frames"], "seconds": args.serve_seconds, "per_camera": per_cam},
+        "saturated": {"frames_per_s": ss["frames_per_s"], "W*H*D/s": sat_whd, "p50_ms": ss["p50_ms"],
+                      "p99_ms": ss["p99_ms"], "outstanding_per_camera": 4},
+        "server": {"paced": paced.stats, "saturated": sat.stats},
+        "config": {"workload": "serve_6cams_kitti2_vga2_720p_1080p", "max_batch": SERVE_BATCH, "slots_per_shape": 2,
+                   "budget_bytes": SERVE_BUDGET, "all_ok": ok},
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": ss["frames_per_s"], "unit": "frames/s",
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "every request is end to end: host buffers in, host buffers out"},
+        # every batch is one sgmf_compute_batch: 13 kernel launches with the default parameters
+        "gpu_launches": 13 * (paced.stats["batches"] + sat.stats["batches"]), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,7 +362,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed"])
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--mixed-distinct", type=int, default=3,
                     help="distinct generated pairs per shape in the mixed batch (reused cyclically)")
     ap.add_argument("--no-tune", action="store_true")
@@ -308,6 +374,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "mixed":
         return run_mixed(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
 
     import numpy as np
     import torch

@@ -279,6 +279,60 @@ size_t sgmf_multi_device_bytes(const sgmf_multi *m);
 /* Frees everything (NULL-safe); waits for the batch's work first. */
 void sgmf_multi_destroy(sgmf_multi *m);
 
+/* ---- Serving: a request loop for several cameras (no counterpart in the paper)
+ * Requests (one pair + LiDAR map in HOST memory, pinned memory recommended)
+ * are submitted from any thread and come back through sgmf_server_poll.
+ * Cameras of equal shape share one queue.  One worker thread owns the GPU
+ * work: whenever a batched context ("slot", max_batch frames with resident
+ * device buffers and its own stream) of a shape is idle it takes every
+ * waiting request of that shape, up to max_batch, and runs copy-in, the
+ * pipeline (one sgmf_compute_batch) and copy-out on the slot's stream.
+ * Requests that arrive meanwhile wait for the next idle slot: batches form
+ * continuously while earlier ones are on the GPU, and the slots of
+ * different shapes (and up to max_slots_per_shape of one shape) overlap on
+ * the device.  Slots are created while their device bytes fit the budget
+ * (admission by device memory).  A frame's result does not depend on which
+ * batch or slot it ran in.  Errors of these calls are reported in
+ * sgmf_last_error(NULL). */
+typedef struct sgmf_server sgmf_server;
+typedef struct {
+    uint64_t submitted, completed;  /* requests */
+    uint64_t batches, batched_frames;
+    int32_t largest_batch;          /* frames in the largest batch so far */
+    int32_t max_concurrent_batches; /* most batches in flight at once */
+    int32_t slots;                  /* slots created */
+    size_t device_bytes, peak_device_bytes, budget_bytes;
+} sgmf_server_counters;
+
+/* Starts the worker on the current device.  p = NULL selects Table II.
+ * 1 <= max_batch <= 256, 1 <= max_slots_per_shape <= 16.  Errors:
+ * SGMF_ERR_ARG, SGMF_ERR_PARAM, SGMF_ERR_OOM. */
+sgmf_status sgmf_server_create(const sgmf_params *p, size_t device_budget_bytes, int max_batch,
+                               int max_slots_per_shape, sgmf_server **out);
+
+/* Registers a camera; returns its id (>= 0) or minus an sgmf_status.  The
+ * first camera of a shape creates that shape's first slot and is refused
+ * with -SGMF_ERR_OOM if it does not fit the remaining budget.  Call from one
+ * thread (cameras may be added while requests run). */
+int sgmf_server_add_camera(sgmf_server *s, int width, int height, int max_disp);
+
+/* Queues one request.  left / right uint8 H x W, lidar float32 H x W or NULL
+ * (no LiDAR), out int16 H x W: host buffers that must stay valid until the
+ * request is returned by sgmf_server_poll.  Returns at once. */
+sgmf_status sgmf_server_submit(sgmf_server *s, int camera, const uint8_t *left, const uint8_t *right,
+                               const float *lidar, int16_t *out, uint64_t tag);
+
+/* Returns 1 and one finished request (tag, camera, status, latency from
+ * submit to the output landing in host memory, in ms), or 0 if none finished
+ * within wait_ms; -SGMF_ERR_ARG for a NULL server.  Any pointer may be NULL. */
+int sgmf_server_poll(sgmf_server *s, int wait_ms, uint64_t *tag, int *camera, int *status, double *latency_ms);
+
+sgmf_status sgmf_server_stats(sgmf_server *s, sgmf_server_counters *out);
+
+/* Finishes every queued and running request, stops the worker, frees all
+ * slots (NULL-safe).  Requests finished but not polled are dropped. */
+void sgmf_server_destroy(sgmf_server *s);
+
 /* The three-view consistency stage alone, without a context and without
  * allocating anything.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory where they call it

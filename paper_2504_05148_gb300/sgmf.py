@@ -34,6 +34,8 @@ EXPORTS = (
     "sgmf_multi_create", "sgmf_multi_frame", "sgmf_multi_classes", "sgmf_multi_class_info",
     "sgmf_multi_autotune", "sgmf_multi_launch", "sgmf_multi_sync", "sgmf_multi_launches",
     "sgmf_multi_device_bytes", "sgmf_multi_destroy",
+    "sgmf_server_create", "sgmf_server_add_camera", "sgmf_server_submit", "sgmf_server_poll",
+    "sgmf_server_stats", "sgmf_server_destroy",
 )
 
 
@@ -51,6 +53,14 @@ class sgmf_params(ctypes.Structure):
 
 class sgmf_tuning(ctypes.Structure):
     _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32)]
+
+
+class sgmf_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("batched_frames", ctypes.c_uint64), ("largest_batch", ctypes.c_int32),
+                ("max_concurrent_batches", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("device_bytes", ctypes.c_size_t), ("peak_device_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
 
 
 class sgmf_shape(ctypes.Structure):
@@ -140,6 +150,13 @@ def lib(path: str | None = None):
         "sgmf_multi_launches": (i, [P]),
         "sgmf_multi_device_bytes": (sz, [P]),
         "sgmf_multi_destroy": (None, [P]),
+        "sgmf_server_create": (i, [prm_p, sz, i, i, ctx_pp]),
+        "sgmf_server_add_camera": (i, [P, i, i, i]),
+        "sgmf_server_submit": (i, [P, i, P, P, P, P, ctypes.c_uint64]),
+        "sgmf_server_poll": (i, [P, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "sgmf_server_stats": (i, [P, ctypes.POINTER(sgmf_server_counters)]),
+        "sgmf_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -338,6 +355,47 @@ def sgmf_multi_device_bytes(m: int) -> int:
 
 def sgmf_multi_destroy(m: int | None) -> None:
     lib().sgmf_multi_destroy(m)
+
+
+def sgmf_server_create(params: Params | None, budget_bytes: int, max_batch: int, max_slots_per_shape: int) -> int:
+    out = ctypes.c_void_p()
+    c = params.to_c() if params is not None else None
+    _check(lib().sgmf_server_create(ctypes.byref(c) if c is not None else None, budget_bytes, max_batch,
+                                    max_slots_per_shape, ctypes.byref(out)), None)
+    return out.value
+
+
+def sgmf_server_add_camera(srv: int, width: int, height: int, max_disp: int) -> int:
+    r = lib().sgmf_server_add_camera(srv, width, height, max_disp)
+    if r < 0:
+        raise SgmfError(-r, sgmf_last_error(None))
+    return r
+
+
+def sgmf_server_submit(srv: int, camera: int, left: int, right: int, lidar: int | None, out: int,
+                       tag: int) -> None:
+    """Host pointers that must stay valid until the request is polled."""
+    _check(lib().sgmf_server_submit(srv, camera, left, right, lidar or None, out, tag), None)
+
+
+def sgmf_server_poll(srv: int, wait_ms: int):
+    """None, or (tag, camera, status, latency_ms) of one finished request."""
+    tag, cam, st, lat = ctypes.c_uint64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    r = lib().sgmf_server_poll(srv, wait_ms, ctypes.byref(tag), ctypes.byref(cam), ctypes.byref(st),
+                               ctypes.byref(lat))
+    if r < 0:
+        raise SgmfError(-r, "sgmf_server_poll")
+    return None if r == 0 else (tag.value, cam.value, st.value, lat.value)
+
+
+def sgmf_server_stats(srv: int) -> dict:
+    c = sgmf_server_counters()
+    _check(lib().sgmf_server_stats(srv, ctypes.byref(c)), None)
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
+def sgmf_server_destroy(srv: int | None) -> None:
+    lib().sgmf_server_destroy(srv)
 
 
 # ---- torch convenience wrapper ------------------------------------------------------

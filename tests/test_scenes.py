@@ -42,3 +42,23 @@ def test_named_workloads():
     assert scenes.by_name("indoor").left.shape == (480, 640)
     s = scenes.by_name("lowlight")
     assert s.left.shape == (720, 1280) and s.D == 192 and s.left.max() <= 40
+
+
+def test_poisson_schedule_rate_and_determinism():
+    from paper_2504_05148_gb300 import serving
+    a = serving.poisson_schedule(25.0, 200.0, 3)
+    b = serving.poisson_schedule(25.0, 200.0, 3)
+    np.testing.assert_array_equal(a, b)
+    assert abs(len(a) / 200.0 - 25.0) < 1.5                  # mean rate (5000 arrivals)
+    gaps = np.diff(a)
+    assert (gaps > 0).all()
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1         # exponential: coefficient of variation 1
+    assert a.max() < 200.0
+
+
+def test_mixed_batch_shapes():
+    from paper_2504_05148_gb300 import scenes as sc
+    s = sc.mixed(4000, 64, 32, 16)
+    assert s.shape == (32, 64) and s.D == 16
+    assert (s.lidar >= 0).all() and np.isfinite(s.lidar).all()
+    assert sc.MIXED_SHAPES == ((640, 480, 64), (1242, 375, 128), (1280, 720, 192), (1920, 1080, 256))
