@@ -105,6 +105,12 @@ def lib():
         L.sgmfo_compute.argtypes = [ctypes.POINTER(_CParams), i, i, i, P, P, P, P,
                                     P, P, P, P, P, P, P, P]
         L.sgmfo_compute.restype = i
+        L.sgmfo_path_banded.argtypes = [i, i, i, i, P, P, i, i, i, i, P]
+        L.sgmfo_aggregate_banded.argtypes = [i, i, i, i, P, P, i, i, i, P]
+        L.sgmfo_aggregate_banded.restype = i
+        L.sgmfo_wta_banded.argtypes = [i, i, i, i, P, P, P, P]
+        L.sgmfo_compute_banded.argtypes = [ctypes.POINTER(_CParams), i, i, i, i, P, P, P, P, P, P, P, P]
+        L.sgmfo_compute_banded.restype = i
         _lib = L
     return _lib
 
@@ -272,3 +278,69 @@ def compute(left: np.ndarray, right: np.ndarray, lidar_f32: np.ndarray | None, D
     if rc != 0:
         raise MemoryError("oracle compute: allocation failed")
     return r
+
+
+# ---- banded SGM (not in the paper: the method restricted to per-pixel bands) ----
+
+ABSENT = 1 << 29
+
+
+def expand_tiles(lo_tiles: np.ndarray, W: int, H: int, tile: int = 16) -> np.ndarray:
+    """Per-pixel band starts from per-tile ones ([ceil(H/tile)][ceil(W/tile)])."""
+    lo_tiles = np.asarray(lo_tiles)
+    ys = np.arange(H) // tile
+    xs = np.arange(W) // tile
+    return np.ascontiguousarray(lo_tiles[ys[:, None], xs[None, :]].astype(np.int16))
+
+
+def path_banded(cv: np.ndarray, lo: np.ndarray, B: int, p1: int, p2: int, rx: int, ry: int) -> np.ndarray:
+    cv = _c(cv, np.int32)
+    lo = _c(lo, np.int16)
+    H, W, D = cv.shape
+    out = np.empty_like(cv)
+    lib().sgmfo_path_banded(W, H, D, B, _p(lo), _p(cv), p1, p2, rx, ry, _p(out))
+    return out
+
+
+def aggregate_banded(cv: np.ndarray, lo: np.ndarray, B: int, p1: int, p2: int, num_paths: int = 8) -> np.ndarray:
+    cv = _c(cv, np.int32)
+    lo = _c(lo, np.int16)
+    H, W, D = cv.shape
+    out = np.empty_like(cv)
+    if lib().sgmfo_aggregate_banded(W, H, D, B, _p(lo), _p(cv), p1, p2, num_paths, _p(out)) != 0:
+        raise MemoryError("oracle aggregate_banded: allocation failed")
+    return out
+
+
+def wta_banded(sv: np.ndarray, lo: np.ndarray, B: int):
+    sv = _c(sv, np.int32)
+    lo = _c(lo, np.int16)
+    H, W, D = sv.shape
+    ds = np.empty((H, W), np.int16)
+    dp = np.empty((H, W), np.int16)
+    lib().sgmfo_wta_banded(W, H, D, B, _p(lo), _p(sv), _p(ds), _p(dp))
+    return ds, dp
+
+
+def compute_banded(left, right, lidar_f32, D: int, B: int, lo: np.ndarray, params: Params | None = None,
+                   volumes: bool = False) -> Result:
+    """The pipeline with aggregation, WTA and check on the bands [lo, lo + B)."""
+    params = params or Params()
+    left = _c(left, np.uint8)
+    right = _c(right, np.uint8)
+    H, W = left.shape
+    lo = _c(lo, np.int16)
+    assert lo.shape == (H, W)
+    li = None if lidar_f32 is None else _c(lidar_f32, np.float32)
+    cp = _CParams(**asdict(params))
+    r = Result(out=np.empty((H, W), np.int16))
+    r.dstar = np.empty((H, W), np.int16)
+    r.dprime = np.empty((H, W), np.int16)
+    if volumes:
+        r.sum = np.empty((H, W, D), np.int32)
+    rc = lib().sgmfo_compute_banded(ctypes.byref(cp), W, H, D, B, _p(lo), _p(left), _p(right), _p(li), _p(r.out),
+                                    _p(r.sum), _p(r.dstar), _p(r.dprime))
+    if rc != 0:
+        raise MemoryError("oracle compute_banded: allocation failed")
+    return r
+

@@ -348,16 +348,17 @@ void sgmfo_subpixel(int W, int H, int D, const int32_t *sv, const int16_t *dstar
  *   |d*_p - d-bar_q| <= tc.
  * The raw map d-bar is used, not d-hat (stated after Eq. 6).  Otherwise the
  * output is invalid (-1).  `mode` selects the ablation variants of Table V. */
-void sgmfo_consistency(int W, int H, const int16_t *dstar, const int16_t *dprime,
-                       const int16_t *dbar, int tc, int rc, int lr_max_diff, int mode,
-                       int16_t *out)
+static void consistency_(int W, int H, const int16_t *dstar, const int16_t *dprime,
+                         const int16_t *dbar, int tc, int rc, int lr_max_diff, int mode,
+                         int need_dprime, int16_t *out)
 {
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             int ds = dstar[(size_t)y * W + x];
             int stereo_ok = 0, lidar_ok = 0;
             int xm = x - ds;
-            if (xm >= 0 && iabs_(ds - dprime[(size_t)y * W + xm]) <= lr_max_diff)
+            if (xm >= 0 && (!need_dprime || dprime[(size_t)y * W + xm] >= 0) &&
+                iabs_(ds - dprime[(size_t)y * W + xm]) <= lr_max_diff)
                 stereo_ok = 1;
             for (int qy = y - rc; qy <= y + rc && !lidar_ok; ++qy) {
                 if (qy < 0 || qy >= H) continue;
@@ -379,6 +380,13 @@ void sgmfo_consistency(int W, int H, const int16_t *dstar, const int16_t *dprime
             }
             out[(size_t)y * W + x] = (int16_t)(ok ? ds : SGMFO_INVALID);
         }
+}
+
+void sgmfo_consistency(int W, int H, const int16_t *dstar, const int16_t *dprime,
+                       const int16_t *dbar, int tc, int rc, int lr_max_diff, int mode,
+                       int16_t *out)
+{
+    consistency_(W, H, dstar, dprime, dbar, tc, rc, lr_max_diff, mode, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -433,6 +441,140 @@ int sgmfo_compute(const sgmfo_params *prm, int W, int H, int D,
     if (dump_cl) memcpy(dump_cl, cl, n * sizeof(uint64_t));
     if (dump_cr) memcpy(dump_cr, cr, n * sizeof(uint64_t));
     if (dump_dhat) memcpy(dump_dhat, dhat, n * sizeof(int16_t));
+    if (dump_sum) memcpy(dump_sum, hv, nv * sizeof(int32_t));
+    if (dump_dstar) memcpy(dump_dstar, dstar, n * sizeof(int16_t));
+    if (dump_dprime) memcpy(dump_dprime, dprime, n * sizeof(int16_t));
+    rc = 0;
+out:
+    free(dbar); free(dhat); free(dstar); free(dprime);
+    free(cl); free(cr); free(hv); free(cv);
+    return rc;
+}
+
+/* ======================================================================== */
+/* Banded SGM.  NOT part of the paper: the method restricted to a disparity
+ * band per pixel, the form a learned band proposal drives.  Pixel p keeps the
+ * disparities [lo_p, lo_p + B) (clipped to [0, D-1]); every quantity of the
+ * method is defined on the band only:
+ *   L_r(p, d) = C(p, d) + min{ L_r(p-r, d), L_r(p-r, d-1) + P1,
+ *                              L_r(p-r, d+1) + P1, m + P2 } - m,
+ *   m = min over the band of p - r of L_r(p - r, k),
+ * where a term whose disparity is outside the band of p - r is left out (as
+ * Eq. 2 leaves out d-1 at d = 0); S(p, d) = sum_r L_r(p, d) on the band of
+ * p; d*_p = argmin over the band of p; d'(x') = argmin over the d with
+ * x' + d < W and d in the band of (x' + d, y) of S(x' + d, y, d), or invalid
+ * (-1) when there is none; the stereo term of Eq. 6 needs a valid d'.
+ * With lo = 0 and B >= D this is exactly the plain method.  Volumes are full
+ * size (H x W x D); cells outside a pixel's band hold SGMFO_ABSENT. */
+#define SGMFO_ABSENT (1 << 29)
+
+static int band_hi_(int lo, int B, int D) { return lo + B < D ? lo + B : D; }   /* exclusive */
+
+void sgmfo_path_banded(int W, int H, int D, int B, const int16_t *lo, const int32_t *cv, int p1,
+                       int p2, int rx, int ry, int32_t *lv)
+{
+    for (int iy = 0; iy < H; ++iy) {
+        int y = ry >= 0 ? iy : H - 1 - iy;
+        for (int ix = 0; ix < W; ++ix) {
+            int x = rx >= 0 ? ix : W - 1 - ix;
+            size_t pi = (size_t)y * W + x, o = pi * D;
+            const int a = lo[pi], ae = band_hi_(a, B, D);
+            for (int d = 0; d < D; ++d) lv[o + d] = SGMFO_ABSENT;
+            int px = x - rx, py = y - ry;
+            if (px < 0 || px >= W || py < 0 || py >= H) {
+                for (int d = a; d < ae; ++d) lv[o + d] = cv[o + d];
+                continue;
+            }
+            size_t qi = (size_t)py * W + px, po = qi * D;
+            const int b = lo[qi], be = band_hi_(b, B, D);
+            int m = 0x7fffffff;
+            for (int k = b; k < be; ++k)
+                if (lv[po + k] < m) m = lv[po + k];
+            for (int d = a; d < ae; ++d) {
+                int best = m + p2;
+                if (d >= b && d < be && lv[po + d] < best) best = lv[po + d];
+                if (d - 1 >= b && d - 1 < be && lv[po + d - 1] + p1 < best) best = lv[po + d - 1] + p1;
+                if (d + 1 >= b && d + 1 < be && lv[po + d + 1] + p1 < best) best = lv[po + d + 1] + p1;
+                lv[o + d] = cv[o + d] + best - m;
+            }
+        }
+    }
+}
+
+int sgmfo_aggregate_banded(int W, int H, int D, int B, const int16_t *lo, const int32_t *cv, int p1,
+                           int p2, int num_paths, int32_t *sv)
+{
+    size_t n = (size_t)W * H * D;
+    int32_t *lv = (int32_t *)malloc(n * sizeof(int32_t));
+    if (lv == NULL) return -1;
+    for (size_t j = 0; j < n; ++j) sv[j] = SGMFO_ABSENT;
+    for (size_t pi = 0; pi < (size_t)W * H; ++pi)
+        for (int d = lo[pi]; d < band_hi_(lo[pi], B, D); ++d) sv[pi * D + d] = 0;
+    for (int i = 0; i < num_paths; ++i) {
+        sgmfo_path_banded(W, H, D, B, lo, cv, p1, p2, kDirs[i][0], kDirs[i][1], lv);
+        for (size_t pi = 0; pi < (size_t)W * H; ++pi)
+            for (int d = lo[pi]; d < band_hi_(lo[pi], B, D); ++d) sv[pi * D + d] += lv[pi * D + d];
+    }
+    free(lv);
+    return 0;
+}
+
+void sgmfo_wta_banded(int W, int H, int D, int B, const int16_t *lo, const int32_t *sv,
+                      int16_t *dstar, int16_t *dprime)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t pi = (size_t)y * W + x;
+            const int32_t *s = sv + pi * D;
+            int bd = lo[pi];
+            for (int d = lo[pi] + 1; d < band_hi_(lo[pi], B, D); ++d)
+                if (s[d] < s[bd]) bd = d;
+            dstar[pi] = (int16_t)bd;
+        }
+    for (int y = 0; y < H; ++y)
+        for (int xr = 0; xr < W; ++xr) {
+            int bd = SGMFO_INVALID, bs = 0x7fffffff;
+            for (int d = 0; d < D && xr + d < W; ++d) {
+                size_t pi = (size_t)y * W + xr + d;
+                if (d < lo[pi] || d >= band_hi_(lo[pi], B, D)) continue;
+                if (sv[pi * D + d] < bs) {
+                    bs = sv[pi * D + d];
+                    bd = d;
+                }
+            }
+            dprime[(size_t)y * W + xr] = (int16_t)bd;
+        }
+}
+
+/* The pipeline of sgmfo_compute with the aggregation, WTA and check on the
+ * bands (lo: H x W band starts).  dump_sum receives the banded S. */
+int sgmfo_compute_banded(const sgmfo_params *prm, int W, int H, int D, int B, const int16_t *lo,
+                         const uint8_t *left, const uint8_t *right, const float *lidar,
+                         int16_t *out, int32_t *dump_sum, int16_t *dump_dstar, int16_t *dump_dprime)
+{
+    size_t n = (size_t)W * H, nv = n * (size_t)D;
+    int16_t *dbar = (int16_t *)malloc(n * sizeof(int16_t));
+    int16_t *dhat = (int16_t *)malloc(n * sizeof(int16_t));
+    int16_t *dstar = (int16_t *)malloc(n * sizeof(int16_t));
+    int16_t *dprime = (int16_t *)malloc(n * sizeof(int16_t));
+    uint64_t *cl = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *cr = (uint64_t *)malloc(n * sizeof(uint64_t));
+    int32_t *hv = (int32_t *)malloc(nv * sizeof(int32_t));
+    int32_t *cv = (int32_t *)malloc(nv * sizeof(int32_t));
+    int rc = -1;
+    if (!dbar || !dhat || !dstar || !dprime || !cl || !cr || !hv || !cv) goto out;
+    sgmfo_lidar(W, H, D, lidar, dbar);
+    sgmfo_census(W, H, left, prm->census, cl);
+    sgmfo_census(W, H, right, prm->census, cr);
+    sgmfo_hamming(W, H, D, cl, cr, sgmfo_census_bits(prm->census), hv);
+    if (prm->semidense)
+        sgmfo_semidense(W, H, D, dbar, hv, prm->ts, prm->rs, dhat);
+    else
+        memcpy(dhat, dbar, n * sizeof(int16_t));
+    sgmfo_ddc(W, H, D, hv, dhat, prm->q1, prm->q2, prm->alpha_num, prm->alpha_den, cv);
+    if (sgmfo_aggregate_banded(W, H, D, B, lo, cv, prm->p1, prm->p2, prm->num_paths, hv) != 0) goto out;
+    sgmfo_wta_banded(W, H, D, B, lo, hv, dstar, dprime);
+    consistency_(W, H, dstar, dprime, dbar, prm->tc, prm->rc, prm->lr_max_diff, prm->consistency, 1, out);
     if (dump_sum) memcpy(dump_sum, hv, nv * sizeof(int32_t));
     if (dump_dstar) memcpy(dump_dstar, dstar, n * sizeof(int16_t));
     if (dump_dprime) memcpy(dump_dprime, dprime, n * sizeof(int16_t));
