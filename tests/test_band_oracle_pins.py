@@ -43,14 +43,17 @@ def test_constant_band_is_the_plain_method_on_a_slice(a0, B):
 
 
 def _brute_banded(C, bands, p1, p2):
-    """min over labelings with label_i in bands[i] of the chain energy, by final label."""
+    """min over labelings with label_i in bands[i] of the chain energy, by final
+    label; a step of one disparity costs P1 only when the previous label is
+    also inside the current band (seen through it), else P2."""
     n, D = C.shape
     best = np.full(D, np.inf)
     for lab in itertools.product(*[range(a, b) for a, b in bands]):
         e = sum(int(C[i, lab[i]]) for i in range(n))
         for i in range(1, n):
             dd = abs(lab[i] - lab[i - 1])
-            e += p1 if dd == 1 else (p2 if dd > 1 else 0)
+            seen = bands[i][0] <= lab[i - 1] < bands[i][1]
+            e += (p1 if seen else p2) if dd == 1 else (p2 if dd > 1 else 0)
         best[lab[-1]] = min(best[lab[-1]], e)
     return best
 
@@ -92,3 +95,17 @@ def test_banded_right_view_search_hand_case():
     # x'=1: (1,0)=50 (3,2)=7 (4,3)=absent, (5,4)=50 -> 2
     # x'=5: (5,0) outside the band [4,6) of x=5 -> invalid
     assert dp[0, 0] == 4 and dp[0, 1] == 2 and dp[0, 5] == -1
+
+
+def test_banded_right_view_search_none_inside():
+    """Cells above a pixel's band never count: here no band holds a cell of the
+    diagonal of x' = 0, so d'(0) is invalid."""
+    lo = np.array([[1, 0, 0]], np.int16)
+    S = np.full((1, 3, 3), oracle.ABSENT, np.int32)
+    S[0, 0, 1] = 5
+    S[0, 1, 0] = 5
+    S[0, 2, 0] = 5
+    _, dp = oracle.wta_banded(S, lo, 1)
+    # x'=0: (0,0) below the band {1} of x=0, (1,1) and (2,2) above the bands {0}
+    assert dp[0, 0] == -1
+    assert dp[0, 1] == 0 and dp[0, 2] == 0
