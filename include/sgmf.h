@@ -204,6 +204,32 @@ sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n
 /* Bytes of device memory the context holds. */
 size_t sgmf_device_bytes(const sgmf_ctx *c);
 
+/* ---- Banded mode (no counterpart in the paper) ---------------------------
+ * The method restricted to a disparity band per pixel: pixel p keeps the
+ * disparities [lo_p, lo_p + band); lo_p is constant on 16 x 16 pixel tiles.
+ * Eq. 2 runs on the bands (a term whose disparity is outside the previous
+ * pixel's band is left out; m is the min over that band), d* is the argmin
+ * over the pixel's band, d'(x') the argmin over the cells (x' + d, d) that
+ * lie inside the bands (-1 where there is none, and the stereo term of Eq. 6
+ * then fails); census, semidensification, Eq. 4 and the check are unchanged.
+ * With band starts 0 and band = max_disp this is the plain method.  Cost,
+ * path costs and S take band / Dp of the plain volumes' memory and work. */
+
+/* A banded context: band = 64 or 128, band <= max_disp.  sgmf_compute on it
+ * fails; use sgmf_compute_banded.  Errors as sgmf_create_batched. */
+sgmf_status sgmf_create_banded(int width, int height, int max_disp, int band, int max_batch, sgmf_ctx **out);
+
+/* sgmf_compute_batch with band starts: band_lo is a DEVICE int16 array
+ * [n][ceil(H / 16)][ceil(W / 16)] (tile rows, then tile columns); values are
+ * clamped to [0, max_disp - band].  subpixel must be 0. */
+sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                const float *lidar, const int16_t *band_lo, int16_t *out);
+
+/* sgmf_debug_stage on a banded context returns COST as uint8 and SUM as
+ * uint16 H x W x band (cell j = disparity lo_p + j; SUM needs no
+ * sgmf_set_debug there).  The context's band width (0 for a plain context): */
+int sgmf_band_width(const sgmf_ctx *c);
+
 /* ---- Launch tuning (no counterpart in the paper) -----------------------
  * Launch shapes only: every choice gives bit-identical results. */
 typedef struct {

@@ -220,6 +220,63 @@ __device__ __forceinline__ void pad_bytes(int D, int lig, uint32_t (&z)[CPL / 4]
   }
 }
 
+// ---- disparity bands (banded mode, not in the paper) -----------------------------
+// In banded mode lane cell j of pixel p stands for disparity lo_p + j, with
+// lo_p constant on 16 x 16 pixel tiles.  A group walking its line tracks the
+// tile of each step; where the band start changes by delta, the previous
+// pixel's path costs are re-indexed: cell j takes old cell j + delta, and the
+// cells that have no old counterpart become absent (kInf, above every real
+// path cost, so they only ever lose a min).  m of the previous pixel stays
+// the min over its own band, as the banded recursion requires.
+struct BandState {
+  const int16_t *lo = nullptr;   // this frame's tile table [th][tw]
+  int tw = 0;
+  int x = 0, y = 0;              // pixel of the next step
+  int dx = 0, dy = 0;            // per-step move
+  int tile = -1, cur = 0;        // tile and band start of the last step
+  uint16_t *buf = nullptr;       // the group's shared scratch, 16 * CPL cells
+};
+
+// Runs on all 32 lanes (full-warp syncs): a group with delta = 0 rewrites its
+// cells in place.  Keeping the shift warp-uniform matters: the recursion's
+// full-warp reductions must never meet a group parked at a partial barrier.
+template <int CPL>
+__device__ __forceinline__ void band_shift(uint32_t (&L)[CPL / 2], int delta, uint16_t *buf, int lig) {
+  constexpr int NW = CPL / 2, B = 16 * CPL;
+  uint32_t *w = reinterpret_cast<uint32_t *>(buf + lig * CPL);
+#pragma unroll
+  for (int i = 0; i < NW; ++i) w[i] = L[i];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const int c0 = lig * CPL + 2 * i + delta;
+    const uint32_t v0 = (unsigned)c0 < (unsigned)B ? (uint32_t)buf[c0] : kInf;
+    const uint32_t v1 = (unsigned)(c0 + 1) < (unsigned)B ? (uint32_t)buf[c0 + 1] : kInf;
+    L[i] = v0 | (v1 << 16);
+  }
+  __syncwarp();
+}
+
+// the band bookkeeping of one step at (bs.x, bs.y), then the move to the next
+// pixel of the line (x wraps for the diagonals).  Called by all 32 lanes.
+template <int CPL>
+__device__ __forceinline__ void band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig) {
+  int delta = 0;
+  if (active) {
+    const int t = (bs.y >> 4) * bs.tw + (bs.x >> 4);
+    if (t != bs.tile) {
+      bs.tile = t;
+      const int nlo = bs.lo[t];
+      delta = nlo - bs.cur;
+      bs.cur = nlo;
+    }
+  }
+  if (__any_sync(kFull, delta != 0)) band_shift<CPL>(L, delta, bs.buf, lig);
+  bs.y += bs.dy;
+  bs.x += bs.dx;
+  bs.x = bs.x >= W ? bs.x - W : (bs.x < 0 ? bs.x + W : bs.x);
+}
+
 // Bounded wait for ring fill g (stage g % S, phase g / S).  The decision is
 // warp-uniform.  On a timeout the warp flags the error, gives every fill it
 // has issued (g .. issued-1) a second bounded wait, and reports false so that
@@ -241,6 +298,8 @@ struct LineArgs {
   void *spill;            // [3][W][H][Dp] elements
   int *err;
   StepConsts sc;
+  const int16_t *lo;      // banded mode: band starts per 16 x 16 tile, [frame][th][tw]
+  int tw, th;
 };
 
 template <int CPL, bool S8, int NWARP>
@@ -268,12 +327,13 @@ __device__ __forceinline__ int line_x(int fam, int k, int y, int W) {
 // in increasing y, the path costs are spilled; up: rows in decreasing y, the
 // spilled L_down of the row is added and the pair sum stored.  FAST: no path
 // restarts inside the chunk (known from the warp-wide min of `togo`).
-template <int CPL, bool S8, int FAM, bool DOWN, bool FAST>
+template <int CPL, bool S8, int FAM, bool DOWN, bool FAST, bool BANDED>
 __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *sstl, int n, uint32_t (&L)[CPL / 2],
                                            uint32_t &mm, int &togo, int &next_len, int seg_full,
                                            uint8_t *&sp, uint16_t *&pp, const uint32_t (&z)[CPL / 4],
                                            const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp,
-                                           bool active, int y_hi, int y_first, int W, uint16_t *part_lane) {
+                                           bool active, int y_hi, int y_first, int W, uint16_t *part_lane,
+                                           BandState &bs, int lig) {
   constexpr int NW = CPL / 2, Dp = 16 * CPL, SB = S8 ? 1 : 2;
   // partial-sum pointer step moving up one row (x - 1, x, x + 1 for families 1, 0, 2)
   constexpr int kDelta = FAM == 0 ? 0 : (FAM == 1 ? -1 : 1);
@@ -283,6 +343,7 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
   for (int i = 0; i < n; ++i) {
     const int r = DOWN ? i : n - 1 - i;       // stage rows are in increasing y
     unpack_u8<CPL>(stl + r * 2 * Dp, z, C);
+    if (BANDED) band_step<CPL>(bs, L, active, W, lig);
     if (!FAST) {
       const bool start = togo == 0;
       const uint32_t keep = start ? 0u : 0xffffffffu;
@@ -318,7 +379,7 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
   if (FAST) togo -= n;
 }
 
-template <int CPL, bool S8, int FAM, int NWARP>
+template <int CPL, bool S8, int FAM, int NWARP, bool BANDED>
 __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant__ LineArgs a) {
   using CF = LineCfg<CPL, S8, NWARP>;
   constexpr int NW = CPL / 2, K = CF::K, S = CF::S, Dp = CF::Dp, SB = CF::SB;
@@ -389,6 +450,17 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   const int seg_full = FAM == 0 ? 0x7fffffff : W;
   const int cost_off = grp * Dp + lig * CPL;                          // lane's cells in a stage row
   const int spill_off = CF::kCost + grp * CF::kSpillLine + lig * CPL * SB;
+  // banded mode: the group's shift scratch follows the barriers
+  BandState bs;
+  if (BANDED) {
+    bs.lo = a.lo + (size_t)f * a.th * a.tw;
+    bs.tw = a.tw;
+    bs.buf = reinterpret_cast<uint16_t *>(smem + CF::kSmem) + (warp * 2 + grp) * Dp;
+    bs.x = x_top;
+    bs.y = 0;
+    bs.dy = 1;
+    bs.dx = FAM == 0 ? 0 : (FAM == 1 ? 1 : -1);
+  }
   // ---- down: r = (0,1), (1,1), (-1,1) ----
   int togo = 0;
   int next_len = FAM == 0 ? 0x7fffffff : (FAM == 1 ? W - x_top : x_top + 1);
@@ -403,11 +475,13 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
       const uint8_t *st = ring + (c % S) * CF::kStage;
       const bool fast = __reduce_min_sync(kFull, (unsigned)(active ? togo : 0x7fffffff)) >= (unsigned)n;
       if (fast)
-        line_chunk<CPL, S8, FAM, true, true>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full, sp,
-                                             pp, z, sc, edge_lo, edge_hi, grp, active, c * K + n - 1, H - 1, W, part);
+        line_chunk<CPL, S8, FAM, true, true, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
+                                                     seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active,
+                                                     c * K + n - 1, H - 1, W, part, bs, lig);
       else
-        line_chunk<CPL, S8, FAM, true, false>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full, sp,
-                                              pp, z, sc, edge_lo, edge_hi, grp, active, c * K + n - 1, H - 1, W, part);
+        line_chunk<CPL, S8, FAM, true, false, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
+                                                      seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active,
+                                                      c * K + n - 1, H - 1, W, part, bs, lig);
       __syncwarp();
     }
   }
@@ -417,6 +491,13 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   // ---- up: r = (0,-1), (-1,-1), (1,-1); emit L_down + L_up ----
   togo = 0;
   next_len = FAM == 0 ? 0x7fffffff : (FAM == 1 ? x_bot + 1 : W - x_bot);
+  if (BANDED) {
+    bs.x = x_bot;
+    bs.y = H - 1;
+    bs.dy = -1;
+    bs.dx = FAM == 0 ? 0 : (FAM == 1 ? -1 : 1);
+    bs.tile = -1;          // the up walk starts afresh (its first step restarts the path)
+  }
   {
     uint8_t *sp = nullptr;
     uint16_t *part_lane = part + lig * CPL;
@@ -430,11 +511,13 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
       const uint8_t *st = ring + (g % S) * CF::kStage;
       const bool fast = __reduce_min_sync(kFull, (unsigned)(active ? togo : 0x7fffffff)) >= (unsigned)n;
       if (fast)
-        line_chunk<CPL, S8, FAM, false, true>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full,
-                                              sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi, H - 1, W, part_lane);
+        line_chunk<CPL, S8, FAM, false, true, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
+                                                      seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi,
+                                                      H - 1, W, part_lane, bs, lig);
       else
-        line_chunk<CPL, S8, FAM, false, false>(st + cost_off, st + spill_off, n, L, mm, togo, next_len, seg_full,
-                                               sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi, H - 1, W, part_lane);
+        line_chunk<CPL, S8, FAM, false, false, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
+                                                       seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active, y_hi,
+                                                       H - 1, W, part_lane, bs, lig);
       __syncwarp();
     }
   }
@@ -459,6 +542,9 @@ struct RowArgs {
   uint16_t *dbg_sum;
   int *err;
   StepConsts sc;
+  const int16_t *lo;      // banded mode: band starts per 16 x 16 tile, [frame][th][tw]
+  int tw, th;
+  uint16_t *sum;          // banded mode: S of every frame, [frame][H][W][Dp]
 };
 
 template <int CPL, bool S8>
@@ -491,12 +577,12 @@ struct RowGeom {
 
 // one chunk of lockstep steps [t_lo, t_hi); SECOND: the half where S is formed;
 // RESTART: the chunk holds the first step of a walk
-template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART>
+template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART, bool BANDED>
 __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, const uint8_t *stg, int xl, int t_lo,
                                           int t_hi, const uint32_t (&z)[CPL / 4], const uint32_t (&kb)[CPL / 2],
                                           const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp, int lig,
                                           uint8_t *spill_lane, int16_t *dstar, int16_t *dprime, int16_t *dsub,
-                                          uint16_t *dbg_lane, uint32_t *merge) {
+                                          uint16_t *dbg_lane, uint32_t *merge, BandState &bs) {
   using CF = RowCfg<CPL, S8>;
   constexpr int NW = CPL / 2, Dp = CF::Dp, SB = CF::SB;
   const uint8_t *cst = stg + lig * CPL;
@@ -508,6 +594,10 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
     const int r = valid ? x - xl : 0;
     uint32_t C[NW];
     unpack_u8<CPL>(cst + r * Dp, z, C);
+    if (BANDED) {
+      bs.x = x;   // rows: the tile follows x (bs.y is the row)
+      band_step<CPL>(bs, w.L, valid, g.W, lig);
+    }
     if (RESTART) {
       // a walk starts at x = 0 (group 0) / x = W-1 (group 1): zero previous vector
       const uint32_t keep = x == (g.fwd ? 0 : g.W - 1) ? 0u : 0xffffffffu;
@@ -533,6 +623,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
       for (int i = 0; i < NW; ++i) Sm[i] += T[i];
     }
     if (dbg_lane != nullptr && valid) store_u16<CPL>(dbg_lane + (size_t)x * Dp, Sm);
+    if (BANDED) continue;   // banded mode: S goes out (dbg_lane), WTA runs in its own kernel
     // keys (S << 8 | d); padding keys have 0xff in the top byte
     uint32_t key[CPL];
 #pragma unroll
@@ -610,7 +701,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
   }
 }
 
-template <int CPL, bool S8, int NP, bool FULLD>
+template <int CPL, bool S8, int NP, bool FULLD, bool BANDED>
 __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs a) {
   using CF = RowCfg<CPL, S8>;
   constexpr int K = CF::K, S = CF::S, Dp = CF::Dp, SB = CF::SB;
@@ -636,6 +727,15 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
   int16_t *dstar = a.dstar + f * fpx, *dprime = a.dprime + f * fpx;
   int16_t *dsub = a.dsub != nullptr ? a.dsub + f * fpx : nullptr;
   uint16_t *dbg_lane = (f == 0 && a.dbg_sum != nullptr) ? a.dbg_sum + g.row * Dp + lig * CPL : nullptr;
+  BandState bs;
+  if (BANDED) {
+    // S of every frame goes out; the shift scratch takes the merge area (unused here)
+    dbg_lane = a.sum + f * fcells + g.row * Dp + lig * CPL;
+    bs.lo = a.lo + (size_t)f * a.th * a.tw;
+    bs.tw = a.tw;
+    bs.y = y;
+    bs.buf = reinterpret_cast<uint16_t *>(merge) + grp * Dp;
+  }
   // the row spill region of this frame
   uint8_t *spill = static_cast<uint8_t *>(a.spill) + f * 4 * fcells * 2 + 3 * fcells * SB;
   uint8_t *spill_lane = spill + (g.row * Dp + lig * CPL) * SB;
@@ -726,8 +826,8 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
     // a walk starts at step delay (group 0) or 0 (group 1)
     const bool restart = t_lo <= g.delay && 0 < t_hi;
 #define ROW_CHUNK(SEC, RS)                                                                                   \
-  row_chunk<CPL, S8, NP, FULLD, SEC, RS>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp, lig,   \
-                                         spill_lane, dstar, dprime, dsub, dbg_lane, merge)
+  row_chunk<CPL, S8, NP, FULLD, SEC, RS, BANDED>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp,  \
+                                                 lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs)
     if (c < c1) {
       if (restart) ROW_CHUNK(false, true); else ROW_CHUNK(false, false);
     } else {
@@ -741,6 +841,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
       __syncwarp();
     }
   }
+  if (BANDED) return;
   if (ok && g.fwd) {
     // right pixels x' = W-1-d whose diagonal leaves the image: slot d of group 0
 #pragma unroll
@@ -775,38 +876,55 @@ static cudaError_t smem_optin(Kern kern, int bytes, bool (&done)[64]) {
   return e;
 }
 
-template <int CPL, bool S8, int FAM, int NWARP>
+template <int CPL, bool S8, int FAM, int NWARP, bool BANDED>
 static cudaError_t launch_line_family_w(const LineArgs &a, int nf, cudaStream_t s) {
   using CF = LineCfg<CPL, S8, NWARP>;
+  constexpr int kSmem = CF::kSmem + (BANDED ? CF::kWarps * 4 * CF::Dp : 0);   // + shift scratch
   static bool done[64] = {};
-  cudaError_t e = smem_optin(k_agg_lines<CPL, S8, FAM, NWARP>, CF::kSmem, done);
+  cudaError_t e = smem_optin(k_agg_lines<CPL, S8, FAM, NWARP, BANDED>, kSmem, done);
   if (e != cudaSuccess) return e;
   const int lines_per_cta = 2 * CF::kWarps;
   dim3 grid((a.k.W + lines_per_cta - 1) / lines_per_cta, nf);
-  k_agg_lines<CPL, S8, FAM, NWARP><<<grid, 32 * CF::kWarps, CF::kSmem, s>>>(a);
+  k_agg_lines<CPL, S8, FAM, NWARP, BANDED><<<grid, 32 * CF::kWarps, kSmem, s>>>(a);
   return cudaGetLastError();
 }
 
-// warps per CTA from the context's tuning (2, 4 or 8)
+// warps per CTA from the context's tuning (2, 4 or 8); the banded variant
+// exists for 4 warps and up to 8 cells per lane (bands of 64 or 128)
 template <int CPL, bool S8, int FAM>
 static cudaError_t launch_line_family(const LineArgs &a, int nf, cudaStream_t s) {
-  switch (a.k.line_warps) {
-    case 2: return launch_line_family_w<CPL, S8, FAM, 2>(a, nf, s);
-    case 8: return launch_line_family_w<CPL, S8, FAM, 8>(a, nf, s);
-    default: return launch_line_family_w<CPL, S8, FAM, 4>(a, nf, s);
+  if (a.lo != nullptr) {
+    if constexpr (CPL <= 8) return launch_line_family_w<CPL, S8, FAM, 4, true>(a, nf, s);
+    return cudaErrorInvalidValue;
   }
+  switch (a.k.line_warps) {
+    case 2: return launch_line_family_w<CPL, S8, FAM, 2, false>(a, nf, s);
+    case 8: return launch_line_family_w<CPL, S8, FAM, 8, false>(a, nf, s);
+    default: return launch_line_family_w<CPL, S8, FAM, 4, false>(a, nf, s);
+  }
+}
+
+// In banded mode (k.band != 0) the kernels see D = Dp = band: lane cells are
+// band positions, never padding.
+static KParams lane_params(const KParams &k) {
+  KParams kk = k;
+  if (k.band) kk.D = k.Dp;
+  return kk;
 }
 
 template <int CPL, bool S8>
 cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
   LineArgs a;
-  a.k = k;
+  a.k = lane_params(k);
   a.cost = b.cost;
   for (int i = 0; i < 3; ++i) a.part[i] = b.part[i];
   a.spill = b.spill;
   a.err = b.err;
   a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
   a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
+  a.lo = k.band ? b.band_lo : nullptr;
+  a.tw = k.tw;
+  a.th = k.th;
   // the three families are independent: one launch each, back to back
   cudaError_t e = launch_line_family<CPL, S8, 0>(a, nf, s);
   if (e != cudaSuccess || k.num_paths != 8) return e;
@@ -815,20 +933,20 @@ cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStrea
   return launch_line_family<CPL, S8, 2>(a, nf, s);
 }
 
-template <int CPL, bool S8, int NP, bool FULLD>
+template <int CPL, bool S8, int NP, bool FULLD, bool BANDED>
 static cudaError_t launch_rows_v(const RowArgs &a, int nf, cudaStream_t s) {
   using CF = RowCfg<CPL, S8>;
   static bool done[64] = {};
-  cudaError_t e = smem_optin(k_agg_rows<CPL, S8, NP, FULLD>, CF::kSmem, done);
+  cudaError_t e = smem_optin(k_agg_rows<CPL, S8, NP, FULLD, BANDED>, CF::kSmem, done);
   if (e != cudaSuccess) return e;
-  k_agg_rows<CPL, S8, NP, FULLD><<<dim3(a.k.H, nf), 32, CF::kSmem, s>>>(a);
+  k_agg_rows<CPL, S8, NP, FULLD, BANDED><<<dim3(a.k.H, nf), 32, CF::kSmem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int CPL, bool S8>
 cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
   RowArgs a;
-  a.k = k;
+  a.k = lane_params(k);
   a.cost = b.cost;
   for (int i = 0; i < 3; ++i) a.part[i] = b.part[i];
   a.spill = b.spill;
@@ -839,10 +957,21 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
   a.err = b.err;
   a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
   a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
+  a.lo = b.band_lo;
+  a.tw = k.tw;
+  a.th = k.th;
+  a.sum = b.band_sum;
+  if (k.band) {
+    if constexpr (CPL <= 8) {
+      if (k.num_paths == 8) return launch_rows_v<CPL, S8, 3, true, true>(a, nf, s);
+      return launch_rows_v<CPL, S8, 1, true, true>(a, nf, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   const bool fulld = k.D == k.Dp;
   if (k.num_paths == 8)
-    return fulld ? launch_rows_v<CPL, S8, 3, true>(a, nf, s) : launch_rows_v<CPL, S8, 3, false>(a, nf, s);
-  return fulld ? launch_rows_v<CPL, S8, 1, true>(a, nf, s) : launch_rows_v<CPL, S8, 1, false>(a, nf, s);
+    return fulld ? launch_rows_v<CPL, S8, 3, true, false>(a, nf, s) : launch_rows_v<CPL, S8, 3, false, false>(a, nf, s);
+  return fulld ? launch_rows_v<CPL, S8, 1, true, false>(a, nf, s) : launch_rows_v<CPL, S8, 1, false, false>(a, nf, s);
 }
 
 }  // namespace sgmf

@@ -167,7 +167,7 @@ static void apply_params(sgmf_ctx *c, const sgmf_params &p) {
 static void free_all(sgmf_ctx *c) {
   void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.dsub, c->b.censL,
                   c->b.censR, c->b.pres, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
-                  c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.err, c->st_left,
+                  c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.band_lo, c->b.band_sum, c->b.err, c->st_left,
                   c->st_right, c->st_lidar, c->st_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -186,7 +186,7 @@ extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx
   return sgmf_create_batched(width, height, max_disp, 1, out);
 }
 
-extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, int max_batch, sgmf_ctx **out) {
+static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch, int band, sgmf_ctx **out) {
   if (!out) return fail(nullptr, SGMF_ERR_ARG, "sgmf_create: out is NULL");
   *out = nullptr;
   if (width < 1 || height < 1 || width > kMaxDim || height > kMaxDim || max_disp < 1 || max_disp > kMaxDisp)
@@ -205,7 +205,14 @@ extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, 
   k.D = max_disp;
   k.DPL = max_disp <= 64 ? 2 : max_disp <= 128 ? 4 : max_disp <= 192 ? 6 : 8;
   k.Dp = 32 * k.DPL;
-  k.MW = k.Dp / 32;
+  k.MW = k.Dp / 32;          // presence-mask words cover [0, D)
+  k.band = band;
+  if (band) {                // lanes and volumes hold the band only
+    k.Dp = band;
+    k.DPL = band / 32;
+    k.tw = (width + 15) / 16;
+    k.th = (height + 15) / 16;
+  }
   k.pitch = (width + 15) / 16 * 16;
   k.line_warps = 4;
   k.cost_px = 128;
@@ -234,6 +241,10 @@ extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, 
   A(dalloc(c, &c->b.cost, nv));
   for (int i = 0; i < 3; ++i) A(dalloc(c, &c->b.part[i], nv * 2));
   A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), 4 * nv * 2));
+  if (band) {
+    A(dalloc(c, &c->b.band_lo, (size_t)k.tw * k.th * max_batch * 2));
+    A(dalloc(c, &c->b.band_sum, nv * 2));
+  }
   A(dalloc(c, &c->b.err, sizeof(int)));
   if (e == cudaSuccess) e = cudaMemset(c->b.err, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -253,6 +264,20 @@ extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, 
   }
   *out = c;
   return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_create_batched(int width, int height, int max_disp, int max_batch, sgmf_ctx **out) {
+  return create_ctx(width, height, max_disp, max_batch, 0, out);
+}
+
+extern "C" sgmf_status sgmf_create_banded(int width, int height, int max_disp, int band, int max_batch,
+                                          sgmf_ctx **out) {
+  if (out) *out = nullptr;
+  if (band != 64 && band != 128)
+    return fail(nullptr, SGMF_ERR_SHAPE, "sgmf_create_banded: band must be 64 or 128 (got %d)", band);
+  if (max_disp < band)
+    return fail(nullptr, SGMF_ERR_SHAPE, "sgmf_create_banded: need band <= max_disp (got %d > %d)", band, max_disp);
+  return create_ctx(width, height, max_disp, max_batch, band, out);
 }
 
 extern "C" void sgmf_destroy(sgmf_ctx *c) {
@@ -301,6 +326,7 @@ extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (c->k.semidense) n += 3;
   if (need_boxc(c->k)) n += 2;
   n += 1;      // consistency
+  if (c->k.band) n += 2;   // band clamp, banded WTA
   return n;
 }
 
@@ -330,6 +356,7 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute: NULL image or output pointer");
   if (n < 1 || n > c->nb)
     return fail(c, SGMF_ERR_ARG, "sgmf_compute_batch: need 1 <= n <= %d frames (got %d)", c->nb, n);
+  if (c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute: a banded context needs sgmf_compute_banded");
   const KParams &k = c->k;
   cudaStream_t s = c->stream;
   c->nrec = 0;
@@ -436,14 +463,14 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
     case SGMF_STAGE_DBAR: case SGMF_STAGE_DHAT: case SGMF_STAGE_DSTAR: case SGMF_STAGE_DPRIME:
     case SGMF_STAGE_DSUB: need = n * 2; break;
     case SGMF_STAGE_CENSUS_L: case SGMF_STAGE_CENSUS_R: need = n * 8; break;
-    case SGMF_STAGE_COST: need = n * k.D; break;
-    case SGMF_STAGE_SUM: need = n * k.D * 2; break;
+    case SGMF_STAGE_COST: need = n * (k.band ? k.band : k.D); break;
+    case SGMF_STAGE_SUM: need = n * (k.band ? k.band : k.D) * 2; break;
     default: return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: unknown stage %d", stage);
   }
   if (bytes < need) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: need %zu bytes, got %zu", need, bytes);
   if (stage == SGMF_STAGE_DSUB && !k.subpixel)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: DSUB needs subpixel = 1");
-  if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum)
+  if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum && !k.band)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: SUM needs sgmf_set_debug(c, 1) before sgmf_compute");
   sgmf_status st = sgmf_sync(c);
   if (st != SGMF_OK) return st;
@@ -469,9 +496,13 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
       break;
     }
     case SGMF_STAGE_COST:
-      CUDA_TRY(c, cudaMemcpy2D(dst, k.D, c->b.cost, k.Dp, k.D, n, cudaMemcpyDeviceToHost));
+      CUDA_TRY(c, cudaMemcpy2D(dst, need / n, c->b.cost, k.Dp, need / n, n, cudaMemcpyDeviceToHost));
       break;
     case SGMF_STAGE_SUM:
+      if (k.band) {   // banded: [H][W][band], cell j = disparity lo_p + j
+        CUDA_TRY(c, cudaMemcpy(dst, c->b.band_sum, need, cudaMemcpyDeviceToHost));
+        break;
+      }
       CUDA_TRY(c, cudaMemcpy2D(dst, (size_t)k.D * 2, c->b.dbg_sum, (size_t)k.Dp * 2, (size_t)k.D * 2, n,
                                cudaMemcpyDeviceToHost));
       break;
@@ -583,3 +614,48 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
   if (best_ms) *best_ms = win_ms;
   return SGMF_OK;
 }
+
+// ---- banded mode ---------------------------------------------------------------
+extern "C" sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                           const float *lidar, const int16_t *band_lo, int16_t *out) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!left || !right || !out || !band_lo) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: NULL pointer");
+  if (!c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: context is not banded (sgmf_create_banded)");
+  if (n < 1 || n > c->nb)
+    return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: need 1 <= n <= %d frames (got %d)", c->nb, n);
+  if (c->k.subpixel) return fail(c, SGMF_ERR_PARAM, "sgmf_compute_banded: subpixel must be 0");
+  const KParams &k = c->k;
+  cudaStream_t s = c->stream;
+  c->nrec = 0;
+  mark(c, "ingest");
+  LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
+  LAUNCH_TRY(c, launch_band_clamp(k, c->b, n, band_lo, s));
+  mark(c, "census");
+  LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
+  if (k.semidense) {
+    mark(c, "boxor_semidense");
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s));
+    mark(c, "semidense");
+    LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
+  }
+  mark(c, "cost");
+  LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
+  mark(c, "agg_lines");
+  LAUNCH_TRY(c, launch_agg_lines(k, c->b, n, c->spill8, s));
+  mark(c, "agg_rows");
+  LAUNCH_TRY(c, launch_agg_rows(k, c->b, n, c->spill8, s));
+  mark(c, "wta");
+  LAUNCH_TRY(c, launch_wta_banded(k, c->b, n, s));
+  if (need_boxc(k)) {
+    mark(c, "boxor_check");
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s));
+  }
+  mark(c, "consistency");
+  LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
+  mark(c, "end");
+  c->computed = true;
+  c->last_n = n;
+  return SGMF_OK;
+}
+
+extern "C" int sgmf_band_width(const sgmf_ctx *c) { return c ? c->k.band : 0; }

@@ -26,7 +26,10 @@ __global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b0, int1
   bool stereo_ok = false, lidar_ok = false;
   if (k.consistency != 2 && k.consistency != 3) {
     const int xm = x - ds;
-    stereo_ok = xm >= 0 && abs(ds - (int)b.dprime[(size_t)y * k.W + xm]) <= k.lr;
+    // (d' is always valid for the plain method; the banded mode marks a right
+    // pixel whose diagonal meets no band with -1, and the term then fails)
+    const int dp = xm >= 0 ? (int)b.dprime[(size_t)y * k.W + xm] : -1;
+    stereo_ok = dp >= 0 && abs(ds - dp) <= k.lr;
   }
   if (k.consistency == 0 || k.consistency == 2) {
     const int lo = max(ds - k.tc, 0), hi = min(ds + k.tc, k.D - 1);

@@ -334,9 +334,6 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 // right-census window is staged in shared memory, the lanes of a warp walk
 // the disparities of one pixel, and the CTA's [PX][Dp] cost rows, assembled
 // in shared memory, leave as 16-byte stores (cells d >= D hold 0).
-struct CostTable {
-  uint8_t v[4][64];   // [q class][H]; class 3 (no prior) is the identity
-};
 
 
 template <typename CT>
@@ -420,14 +417,7 @@ static void launch_cost_t(const KParams &k, const Buffers &b, int nf, const Cost
 }
 
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
-  CostTable tab;
-  const int qs[3] = {0, k.q1, k.q2};
-  for (int c = 0; c < 3; ++c)
-    for (int h = 0; h < 64; ++h) {
-      const long v = ((long)(k.b - k.a) * h + (long)k.a * qs[c] + k.b / 2) / k.b;
-      tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
-    }
-  for (int h = 0; h < 64; ++h) tab.v[3][h] = (uint8_t)h;
+  const CostTable tab = cost_table(k);
   if (k.census == 1)
     launch_cost_t<uint64_t>(k, b, nf, tab, s);
   else

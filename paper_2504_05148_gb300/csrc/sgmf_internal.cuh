@@ -36,7 +36,9 @@ struct KParams {
   int ts, rs, tc, rc, lr;
   int census, semidense, consistency, num_paths, subpixel;
   int nbits;
-  int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA                  // census bits (31 or 62)
+  int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA
+  int band;                   // banded mode: band width B (= Dp); 0 = the plain method
+  int tw, th;                 // banded mode: 16 x 16 band tiles per row / column                  // census bits (31 or 62)
 };
 
 struct Buffers {   // base pointers of frame 0
@@ -50,6 +52,8 @@ struct Buffers {   // base pointers of frame 0
   void *spill;                // 4 regions (vertical, diag, anti-diag, rows) of H*W*Dp elements
   uint16_t *dbg_sum;          // [H][W][Dp] or null
   int *err;                   // device error word
+  int16_t *band_lo;           // banded mode: band start per tile, [frame][th][tw] (clamped copy)
+  uint16_t *band_sum;         // banded mode: S, [frame][H][W][Dp]
 };
 
 // per-frame element counts
@@ -79,6 +83,8 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
   for (int i = 0; i < 3; ++i) v.part[i] = b.part[i] + f * cells;
   v.spill = static_cast<uint8_t *>(b.spill) + f * 4 * cells * 2;
   v.dbg_sum = (b.dbg_sum != nullptr && f == 0) ? b.dbg_sum : nullptr;
+  v.band_lo = b.band_lo ? b.band_lo + (size_t)f * k.th * k.tw : nullptr;
+  v.band_sum = b.band_sum ? b.band_sum + f * cells : nullptr;
   return v;
 }
 
@@ -151,6 +157,24 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 struct TmaMaps;   // opaque holder of the two image tensor maps (sgmf_front.cu)
 
 // Every launcher covers frames [0, nf) of the context's buffers.
+// C-bar of Eq. 4 by q class (0: d = prior, 1: |d - prior| = 1, 2: farther)
+// and Hamming distance H; class 3 (no prior) is the identity, C-bar = H:
+//   C-bar = floor(((b - a) H + a q + floor(b / 2)) / b),  q = 0 / q1 / q2.
+struct CostTable {
+  uint8_t v[4][64];
+};
+inline CostTable cost_table(const KParams &k) {
+  CostTable tab;
+  const int qs[3] = {0, k.q1, k.q2};
+  for (int c = 0; c < 3; ++c)
+    for (int h = 0; h < 64; ++h) {
+      const long v = ((long)(k.b - k.a) * h + (long)k.a * qs[c] + k.b / 2) / k.b;
+      tab.v[c][h] = (uint8_t)(v > 255 ? 255 : v);
+    }
+  for (int h = 0; h < 64; ++h) tab.v[3][h] = (uint8_t)h;
+  return tab;
+}
+
 cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint8_t *left,
                           const uint8_t *right, const float *lidar, cudaStream_t s);
 cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
@@ -161,6 +185,9 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
+cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const int16_t *lo_in, cudaStream_t s);
+cudaError_t launch_cost_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+cudaError_t launch_wta_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);
 
 // host: parameter rules of sgmf_set_params (SGMF_OK or SGMF_ERR_PARAM with a reason)

@@ -36,6 +36,7 @@ EXPORTS = (
     "sgmf_multi_device_bytes", "sgmf_multi_destroy",
     "sgmf_server_create", "sgmf_server_add_camera", "sgmf_server_submit", "sgmf_server_poll",
     "sgmf_server_stats", "sgmf_server_destroy",
+    "sgmf_create_banded", "sgmf_compute_banded", "sgmf_band_width",
 )
 
 
@@ -157,6 +158,9 @@ def lib(path: str | None = None):
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "sgmf_server_stats": (i, [P, ctypes.POINTER(sgmf_server_counters)]),
         "sgmf_server_destroy": (None, [P]),
+        "sgmf_create_banded": (i, [i, i, i, i, i, ctx_pp]),
+        "sgmf_compute_banded": (i, [P, i, P, P, P, P, P]),
+        "sgmf_band_width": (i, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -285,6 +289,21 @@ def sgmf_check_static(width: int, height: int, max_disp: int, params: Params, ds
                                    stream or None), None)
 
 
+def sgmf_create_banded(width: int, height: int, max_disp: int, band: int, max_batch: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().sgmf_create_banded(width, height, max_disp, band, max_batch, ctypes.byref(out)), None)
+    return out.value
+
+
+def sgmf_compute_banded(ctx: int, n: int, left: int, right: int, lidar: int | None, band_lo: int, out: int) -> None:
+    """Device pointers; band_lo int16 [n][ceil(H/16)][ceil(W/16)]."""
+    _check(lib().sgmf_compute_banded(ctx, n, left, right, lidar or None, band_lo, out), ctx)
+
+
+def sgmf_band_width(ctx: int) -> int:
+    return lib().sgmf_band_width(ctx)
+
+
 def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int) -> None:
     t = sgmf_tuning(line_warps, cost_px)
     _check(lib().sgmf_set_tuning(ctx, ctypes.byref(t)), ctx)
@@ -404,10 +423,12 @@ class Context:
     """Owns one sgmf context for a (width, height, max_disp) shape."""
 
     def __init__(self, width: int, height: int, max_disp: int, params: Params | None = None,
-                 stream=None, max_batch: int = 1):
+                 stream=None, max_batch: int = 1, band: int = 0):
         self.W, self.H, self.D = width, height, max_disp
         self.max_batch = max_batch
-        self.handle = sgmf_create_batched(width, height, max_disp, max_batch)
+        self.band = band
+        self.handle = (sgmf_create_banded(width, height, max_disp, band, max_batch) if band
+                       else sgmf_create_batched(width, height, max_disp, max_batch))
         if params is not None:
             sgmf_set_params(self.handle, params)
         if stream is not None:
@@ -439,6 +460,21 @@ class Context:
                 raise ValueError(f"lidar must be a contiguous CUDA float32 {shape} tensor or None")
             lp = lidar.data_ptr()
         sgmf_compute_batch(self.handle, n, left.data_ptr(), right.data_ptr(), lp, out.data_ptr())
+
+    def compute_banded(self, left, right, lidar, band_lo, out) -> None:
+        """torch CUDA tensors as in compute(), plus band_lo: int16 (n, ceil(H/16), ceil(W/16))
+        (or without the frame axis for one frame)."""
+        shape = tuple(left.shape)
+        n = 1 if len(shape) == 2 else shape[0]
+        th, tw = (self.H + 15) // 16, (self.W + 15) // 16
+        if str(band_lo.dtype) != "torch.int16" or not band_lo.is_cuda or not band_lo.is_contiguous() \
+                or band_lo.numel() != n * th * tw:
+            raise ValueError(f"band_lo must be a contiguous CUDA int16 tensor of {n} x {th} x {tw}")
+        for t in (left, right, out):
+            if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError("left, right and out must be contiguous CUDA tensors of one shape")
+        sgmf_compute_banded(self.handle, n, left.data_ptr(), right.data_ptr(),
+                            lidar.data_ptr() if lidar is not None else None, band_lo.data_ptr(), out.data_ptr())
 
     def compute_host(self, left, right, lidar, out) -> None:
         """numpy arrays (H, W) or (n, H, W); blocks until `out` holds the result."""
@@ -472,7 +508,8 @@ class Context:
             SGMF_STAGE_DSTAR: (np.int16, shape2), SGMF_STAGE_DPRIME: (np.int16, shape2),
             SGMF_STAGE_DSUB: (np.int16, shape2),
             SGMF_STAGE_CENSUS_L: (np.uint64, shape2), SGMF_STAGE_CENSUS_R: (np.uint64, shape2),
-            SGMF_STAGE_COST: (np.uint8, shape2 + (self.D,)), SGMF_STAGE_SUM: (np.uint16, shape2 + (self.D,)),
+            SGMF_STAGE_COST: (np.uint8, shape2 + (self.band or self.D,)),
+            SGMF_STAGE_SUM: (np.uint16, shape2 + (self.band or self.D,)),
         }[stage]
         a = np.empty(spec[1], spec[0])
         sgmf_debug_stage(self.handle, stage, a.ctypes.data, a.nbytes)
