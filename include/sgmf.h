@@ -225,6 +225,83 @@ sgmf_status sgmf_create_banded(int width, int height, int max_disp, int band, in
 sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
                                 const float *lidar, const int16_t *band_lo, int16_t *out);
 
+/* The two halves of sgmf_compute_banded, for callers that choose the bands
+ * from the semidensified map: sgmf_compute_front runs ingest, census and
+ * semidensification of n frames; the prior of Eq. 4 (d-hat, or d-bar for
+ * DSGM) is then in the DEVICE buffer sgmf_prior_device(c), int16
+ * [frame][H][W] (stream-ordered: read it on the context's stream);
+ * sgmf_compute_banded_back(c, n, band_lo, out) finishes the same n frames. */
+sgmf_status sgmf_compute_front(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                               const float *lidar);
+const int16_t *sgmf_prior_device(const sgmf_ctx *c);
+sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_t *band_lo, int16_t *out);
+
+/* ---- Band-proposal network (no counterpart in the paper) -------------------
+ * A six-layer 3x3 CNN with 32 channels at quarter resolution (H4 =
+ * ceil(H/4), W4 = ceil(W/4)) proposes a band per pixel from the left image
+ * and d-hat.  Its convolutions run on the tensor cores (BF16 operands, FP32
+ * accumulation).  All pointers are DEVICE pointers; every call is
+ * asynchronous on `stream` (NULL = legacy default stream) and returns
+ * SGMF_ERR_ARG for bad sizes or NULL buffers.  Tensors are channel-last:
+ * activations bf16 [n][h][w][32]; weights bf16 [co][ky][kx][ci] (32 x 3 x 3 x
+ * 32); bias f32 [32].  `err` is a device int that a bounded wait sets to
+ * SGMF_ERR_TIMEOUT (6). */
+
+/* Pack weights into the tensor-core operand images (18432 bytes each):
+ * packed_fwd for sgmf_bn_conv forward, packed_dgrad (the kernel rotated by
+ * 180 degrees, in and out channels swapped) for the data gradient.  Either
+ * output may be NULL. */
+sgmf_status sgmf_bn_pack(const uint16_t *w, uint16_t *packed_fwd, uint16_t *packed_dgrad, void *stream);
+
+/* y = conv3x3(x) with zero padding: + bias (or NULL), ReLU if relu, then
+ * zeroed where mask (bf16 activations, or NULL) is not > 0; written as bf16
+ * to y and / or f32 to yf (either may be NULL, not both).  With packed_dgrad
+ * weights, no bias, no ReLU and the layer input as mask this is the data
+ * gradient through conv + ReLU. */
+sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, const uint16_t *packed, const float *bias,
+                         int relu, const uint16_t *mask, uint16_t *y, float *yf, int *err, void *stream);
+
+/* Weight gradient: dw[co][ky][kx][ci] += sum_p dy[p][co] x[p + (ky-1, kx-1)][ci]
+ * and db[co] += sum_p dy[p][co] (f32, accumulated: zero them first). */
+sgmf_status sgmf_bn_wgrad(int n, int h, int w, const uint16_t *x, const uint16_t *dy, float *dw, float *db,
+                          int *err, void *stream);
+
+/* Network input from left uint8 [n][H][W] and d-hat int16 [n][H][W]: per 4 x 4
+ * block (clipped at the border) channel 0 = mean(left) / 255 - 0.5, 1 = mean
+ * of the valid d-hat / max_disp (0 without one), 2 = valid d-hat / 16; the
+ * other channels 0.  x: bf16 [n][H4][W4][32]. */
+sgmf_status sgmf_bn_input(int n, int width, int height, int max_disp, const uint8_t *left, const int16_t *dhat,
+                          uint16_t *x, void *stream);
+
+/* Training labels from disparity maps disp int16 [n][H][W] (-1 invalid): per
+ * quarter pixel lohi[2i] / lohi[2i+1] = min / max of the valid disparities
+ * of its 4 x 4 block (-1 / -1 without one); *count += labelled pixels. */
+sgmf_status sgmf_bn_labels(int n, int width, int height, const int16_t *disp, int16_t *lohi, int *count,
+                           void *stream);
+
+/* Band loss over npix quarter pixels (out: f32 [npix][32], the last layer):
+ * centre c = D o0, half-width w = 8 + 40 sigmoid(o1), confidence q =
+ * sigmoid(o2); per labelled pixel lam_c |c - c_t| / D + lam_w |w - w_t| / D +
+ * BCE(q, y) with c_t = (lo + hi) / 2, w_t = clamp((hi - lo) / 2 + 2, 8, 48),
+ * y = [c - w, c + w] covers [lo, hi]; mean over *count.  grad: bf16
+ * [npix][32] (channels 0..2); *loss += the loss. */
+sgmf_status sgmf_bn_loss(long long npix, int max_disp, const float *out, const int16_t *lohi, const int *count,
+                         uint16_t *grad, float *loss, float lam_c, float lam_w, void *stream);
+
+/* Adam on count f32 parameters (bias-corrected, step >= 1); w_bf16 (or NULL)
+ * receives the bf16 copy. */
+sgmf_status sgmf_bn_adam(int count, float *w, float *m, float *v, const float *g, float lr, float b1, float b2,
+                         float eps, int step, uint16_t *w_bf16, void *stream);
+
+/* Band starts from the network output out (f32 [n][H4][W4][32]) for a
+ * banded context of width `band`: per 16 x 16 tile the union [lo, hi] of the
+ * pixels' bands [c - w, c + w], start round((lo + hi) / 2) - band / 2 clamped
+ * to [0, max_disp - band] into lo_tiles int16 [n][ceil(H/16)][ceil(W/16)];
+ * *uncertain += tiles whose smallest confidence is below conf_min or whose
+ * union is wider than the band. */
+sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp, int band, float conf_min, const float *out,
+                          int16_t *lo_tiles, int *uncertain, void *stream);
+
 /* sgmf_debug_stage on a banded context returns COST as uint8 and SUM as
  * uint16 H x W x band (cell j = disparity lo_p + j; SUM needs no
  * sgmf_set_debug there).  The context's band width (0 for a plain context): */

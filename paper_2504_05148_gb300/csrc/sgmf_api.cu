@@ -19,6 +19,7 @@ using namespace sgmf;
 struct sgmf_ctx {
   int device = 0;
   int nb = 1;                  // frames the buffers hold (batch capacity)
+  int front_n = 0;             // frames whose front half (sgmf_compute_front) awaits the back half
   KParams k{};
   sgmf_params prm{};
   cudaStream_t stream = nullptr;
@@ -616,20 +617,18 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
 }
 
 // ---- banded mode ---------------------------------------------------------------
-extern "C" sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
-                                           const float *lidar, const int16_t *band_lo, int16_t *out) {
+extern "C" sgmf_status sgmf_compute_front(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                          const float *lidar) {
   if (!c) return SGMF_ERR_ARG;
-  if (!left || !right || !out || !band_lo) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: NULL pointer");
-  if (!c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: context is not banded (sgmf_create_banded)");
+  if (!left || !right) return fail(c, SGMF_ERR_ARG, "sgmf_compute_front: NULL image pointer");
+  if (!c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute_front: context is not banded (sgmf_create_banded)");
   if (n < 1 || n > c->nb)
-    return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: need 1 <= n <= %d frames (got %d)", c->nb, n);
-  if (c->k.subpixel) return fail(c, SGMF_ERR_PARAM, "sgmf_compute_banded: subpixel must be 0");
+    return fail(c, SGMF_ERR_ARG, "sgmf_compute_front: need 1 <= n <= %d frames (got %d)", c->nb, n);
   const KParams &k = c->k;
   cudaStream_t s = c->stream;
   c->nrec = 0;
   mark(c, "ingest");
   LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
-  LAUNCH_TRY(c, launch_band_clamp(k, c->b, n, band_lo, s));
   mark(c, "census");
   LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
   if (k.semidense) {
@@ -638,6 +637,26 @@ extern "C" sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *le
     mark(c, "semidense");
     LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
   }
+  c->front_n = n;
+  return SGMF_OK;
+}
+
+extern "C" const int16_t *sgmf_prior_device(const sgmf_ctx *c) {
+  if (!c) return nullptr;
+  return c->k.semidense ? c->b.dhat : c->b.dbar;
+}
+
+extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_t *band_lo, int16_t *out) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!out || !band_lo) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded_back: NULL pointer");
+  if (!c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded_back: context is not banded");
+  if (n < 1 || n != c->front_n)
+    return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded_back: needs the %d frames of the last sgmf_compute_front (got %d)",
+                c->front_n, n);
+  if (c->k.subpixel) return fail(c, SGMF_ERR_PARAM, "sgmf_compute_banded: subpixel must be 0");
+  const KParams &k = c->k;
+  cudaStream_t s = c->stream;
+  LAUNCH_TRY(c, launch_band_clamp(k, c->b, n, band_lo, s));
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
   mark(c, "agg_lines");
@@ -655,7 +674,18 @@ extern "C" sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *le
   mark(c, "end");
   c->computed = true;
   c->last_n = n;
+  c->front_n = 0;
   return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                           const float *lidar, const int16_t *band_lo, int16_t *out) {
+  if (!c) return SGMF_ERR_ARG;
+  if (!out || !band_lo) return fail(c, SGMF_ERR_ARG, "sgmf_compute_banded: NULL pointer");
+  if (c->k.subpixel) return fail(c, SGMF_ERR_PARAM, "sgmf_compute_banded: subpixel must be 0");
+  sgmf_status st = sgmf_compute_front(c, n, left, right, lidar);
+  if (st != SGMF_OK) return st;
+  return sgmf_compute_banded_back(c, n, band_lo, out);
 }
 
 extern "C" int sgmf_band_width(const sgmf_ctx *c) { return c ? c->k.band : 0; }

@@ -37,6 +37,9 @@ EXPORTS = (
     "sgmf_server_create", "sgmf_server_add_camera", "sgmf_server_submit", "sgmf_server_poll",
     "sgmf_server_stats", "sgmf_server_destroy",
     "sgmf_create_banded", "sgmf_compute_banded", "sgmf_band_width",
+    "sgmf_compute_front", "sgmf_prior_device", "sgmf_compute_banded_back",
+    "sgmf_bn_pack", "sgmf_bn_conv", "sgmf_bn_wgrad", "sgmf_bn_input", "sgmf_bn_labels", "sgmf_bn_loss",
+    "sgmf_bn_adam", "sgmf_bn_tiles",
 )
 
 
@@ -161,6 +164,18 @@ def lib(path: str | None = None):
         "sgmf_create_banded": (i, [i, i, i, i, i, ctx_pp]),
         "sgmf_compute_banded": (i, [P, i, P, P, P, P, P]),
         "sgmf_band_width": (i, [P]),
+        "sgmf_compute_front": (i, [P, i, P, P, P]),
+        "sgmf_prior_device": (P, [P]),
+        "sgmf_compute_banded_back": (i, [P, i, P, P]),
+        "sgmf_bn_pack": (i, [P, P, P, P]),
+        "sgmf_bn_conv": (i, [i, i, i, P, P, P, i, P, P, P, P, P]),
+        "sgmf_bn_wgrad": (i, [i, i, i, P, P, P, P, P, P]),
+        "sgmf_bn_input": (i, [i, i, i, i, P, P, P, P]),
+        "sgmf_bn_labels": (i, [i, i, i, P, P, P, P]),
+        "sgmf_bn_loss": (i, [ctypes.c_longlong, i, P, P, P, P, P, ctypes.c_float, ctypes.c_float, P]),
+        "sgmf_bn_adam": (i, [i, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i, P,
+                             P]),
+        "sgmf_bn_tiles": (i, [i, i, i, i, i, ctypes.c_float, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -302,6 +317,60 @@ def sgmf_compute_banded(ctx: int, n: int, left: int, right: int, lidar: int | No
 
 def sgmf_band_width(ctx: int) -> int:
     return lib().sgmf_band_width(ctx)
+
+
+def sgmf_compute_front(ctx: int, n: int, left: int, right: int, lidar: int | None) -> None:
+    _check(lib().sgmf_compute_front(ctx, n, left, right, lidar or None), ctx)
+
+
+def sgmf_prior_device(ctx: int) -> int:
+    return lib().sgmf_prior_device(ctx)
+
+
+def sgmf_compute_banded_back(ctx: int, n: int, band_lo: int, out: int) -> None:
+    _check(lib().sgmf_compute_banded_back(ctx, n, band_lo, out), ctx)
+
+
+# band-proposal network kernels (device pointers; asynchronous on `stream`)
+def sgmf_bn_pack(w: int, packed_fwd: int | None, packed_dgrad: int | None, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_pack(w, packed_fwd or None, packed_dgrad or None, stream or None), None)
+
+
+def sgmf_bn_conv(n: int, h: int, w: int, x: int, packed: int, bias: int | None, relu: bool, mask: int | None,
+                 y: int | None, yf: int | None, err: int, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_conv(n, h, w, x, packed, bias or None, int(bool(relu)), mask or None, y or None,
+                              yf or None, err, stream or None), None)
+
+
+def sgmf_bn_wgrad(n: int, h: int, w: int, x: int, dy: int, dw: int, db: int, err: int,
+                  stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_wgrad(n, h, w, x, dy, dw, db, err, stream or None), None)
+
+
+def sgmf_bn_input(n: int, width: int, height: int, max_disp: int, left: int, dhat: int, x: int,
+                  stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_input(n, width, height, max_disp, left, dhat, x, stream or None), None)
+
+
+def sgmf_bn_labels(n: int, width: int, height: int, disp: int, lohi: int, count: int,
+                   stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_labels(n, width, height, disp, lohi, count, stream or None), None)
+
+
+def sgmf_bn_loss(npix: int, max_disp: int, out: int, lohi: int, count: int, grad: int, loss: int,
+                 lam_c: float = 1.0, lam_w: float = 0.25, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_loss(npix, max_disp, out, lohi, count, grad, loss, lam_c, lam_w, stream or None), None)
+
+
+def sgmf_bn_adam(count: int, w: int, m: int, v: int, g: int, lr: float, b1: float, b2: float, eps: float,
+                 step: int, w_bf16: int | None, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_adam(count, w, m, v, g, lr, b1, b2, eps, step, w_bf16 or None, stream or None), None)
+
+
+def sgmf_bn_tiles(n: int, width: int, height: int, max_disp: int, band: int, conf_min: float, out: int,
+                  lo_tiles: int, uncertain: int, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_tiles(n, width, height, max_disp, band, conf_min, out, lo_tiles, uncertain,
+                               stream or None), None)
 
 
 def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int) -> None:
