@@ -262,6 +262,20 @@ def kitti(seed: int = 2000, beams: int = 64) -> Scene:
     return Scene(f"kitti_1242x375_d128_{beams}beam", seed, D, left, right, lid, truth)
 
 
+def street(seed: int, W: int, H: int, D: int, beams: int = 64) -> Scene:
+    """The KITTI-shaped street scene at any size: ground-plane and object
+    disparities scale with D / 128 (the band proposal's training pairs at
+    1242 x 375 D = 128 and its evaluation pairs at 1920 x 1080 D = 256)."""
+    rng = _rng(seed)
+    s = D / 128.0
+    layers = _street_layers(rng, H, W, 100.0 * s, 20, 115.0 * s)
+    base = texture(rng, H, W)
+    fill = texture(rng, H, W)
+    left, right, truth = render(rng, layers, H, W, base, fill, 2.0)
+    lid = _beam_lidar(rng, truth, 64, 64 // beams, 0.29, 0.01, D)
+    return Scene(f"street_{W}x{H}_d{D}", seed, D, left, right, lid, truth)
+
+
 def lowlight(seed: int = 3300) -> Scene:
     """1280x720, D=192, low-light pair: intensities 0..40, N(0, 3) noise."""
     rng = _rng(seed)
