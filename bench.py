@@ -3,6 +3,7 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
     python bench.py --workload mixed [--steps K] [--warmup W]
     python bench.py --workload serve [--serve-seconds T]
+    python bench.py --workload learned [--eval-frames N] [--band 64|128]
 
 Workload: 1242 x 375 stereo pairs with D = 128 and 64-beam LiDAR (about 5 %
 density), the KITTI-shaped synthetic scene of paper_2504_05148_gb300.scenes;
@@ -24,6 +25,12 @@ cameras (2 x 1242x375 D=128, 2 x 640x480 D=64, 1280x720 D=192,
 1920x1080 D=256) at 10-30 Hz with Poisson jitter: p50/p99 latency from
 submit (host buffers) to the output in host memory; then the same cameras
 with 4 requests each kept outstanding, for the saturated frames/s.
+
+--workload learned: the banded method driven by the trained band-proposal
+network against the plain full-range method at 1920x1080 D=256 on unseen
+street scenes: W*H*D/s of each (the full range D is counted for both), the
+fraction of the plain method's valid pixels that the learned output loses or
+moves by more than one disparity, and the fallback rate.
 """
 from __future__ import annotations
 
@@ -353,6 +360,100 @@ def run_serve(args, rank, world):
     return 0
 
 
+def _gen_street(args):
+    from paper_2504_05148_gb300 import scenes
+    s = scenes.street(*args)
+    return s.left, s.right, s.lidar
+
+
+def run_learned(args, rank, world):
+    """Learned bands vs the plain method at 1920x1080 D=256 (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import multiprocessing as mp
+    W_, H_, D_ = 1920, 1080, 256
+    jobs = [(6000 + i, W_, H_, D_) for i in range(args.eval_frames)]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:   # before any GPU call
+        frames = pool.map(_gen_street, jobs)
+    import numpy as np
+    import torch
+    from paper_2504_05148_gb300 import build as _build
+    _build.build()
+    from paper_2504_05148_gb300 import bandnet, sgmf
+    dev = torch.device("cuda", 0)
+    net = bandnet.BandNet(seed=1)
+    wpath = os.path.join(ROOT, "paper_2504_05148_gb300", "weights", "bandnet_street.npz")
+    if not os.path.exists(wpath):
+        print(json.dumps({"metric": "learned band", "unavailable": f"no trained weights at {wpath}"}))
+        return 0
+    net.load(wpath)
+    dl = [torch.from_numpy(f[0][None]).to(dev) for f in frames]
+    dr = [torch.from_numpy(f[1][None]).to(dev) for f in frames]
+    dli = [torch.from_numpy(f[2][None]).to(dev) for f in frames]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    plain = sgmf.Context(W_, H_, D_)
+    learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
+                                 fallback_frac=args.fallback_frac)
+    outp = [torch.empty((1, H_, W_), dtype=torch.int16, device=dev) for _ in frames]
+    outl = [torch.empty((1, H_, W_), dtype=torch.int16, device=dev) for _ in frames]
+
+    def timed(fn, i):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn(i)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    run_p = lambda i: plain.compute(dl[i][0], dr[i][0], dli[i][0], outp[i][0])
+    run_l = lambda i: learned.compute(dl[i], dr[i], dli[i], outl[i])
+    for i in range(min(len(frames), max(args.warmup, 1))):
+        run_p(i)
+        run_l(i)
+    torch.cuda.synchronize()
+    learned.stats = {k: 0 for k in learned.stats}
+    clocks = ClockSampler(0)
+    clocks.start()
+    tp, tl = [], []
+    for _ in range(args.steps_learned):
+        for i in range(len(frames)):
+            tp.append(timed(run_p, i))
+            tl.append(timed(run_l, i))
+    clk = clocks.stop()
+    plain.sync()
+    learned.sync()
+    dis = [bandnet.disagreement(outl[i].cpu().numpy()[0], outp[i].cpu().numpy()[0]) for i in range(len(frames))]
+    whd = W_ * H_ * D_
+    vp, vl = whd / (np.mean(tp) * 1e-3), whd / (np.mean(tl) * 1e-3)
+    st = learned.stats
+    line = {
+        "metric": "W*H*D/s at 1920x1080 D=256, learned band vs plain full range", "value": vl, "unit": UNIT,
+        "n_gpus": 1, "steps": len(tl), "warmup": args.warmup, "ms_per_step": float(np.mean(tl)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16 (SGM), bf16 (network)",
+        "data": "synthetic",
+        "learned": {"W*H*D/s": vl, "ms_per_frame": float(np.mean(tl)), "band": args.band,
+                    "speedup_vs_plain": vl / vp, "px_off_by_more_than_1": float(np.mean(dis)),
+                    "px_off_by_more_than_1_max_frame": float(np.max(dis)),
+                    "fallback_rate": st["fallback_frames"] / max(st["frames"], 1),
+                    "uncertain_tile_fraction": st["uncertain_tiles"] / max(st["tiles"], 1),
+                    "conf_min": args.conf_min, "fallback_frac": args.fallback_frac},
+        "plain": {"W*H*D/s": vp, "ms_per_frame": float(np.mean(tp))},
+        "config": {"workload": "street_1920x1080_d256_unseen_seeds", "frames": len(frames),
+                   "network": "6 x conv3x3, 32 ch, quarter resolution, bf16/f32 on tcgen05",
+                   "weights": os.path.relpath(wpath, ROOT), "batch": 1,
+                   "l2": "flushed by a 512 MiB write before every frame"},
+        "roofline": None, "cpu_baseline": None,
+        "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    learned.close()
+    plain.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,7 +463,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve"])
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve", "learned"])
+    ap.add_argument("--eval-frames", type=int, default=6)
+    ap.add_argument("--steps-learned", type=int, default=3)
+    ap.add_argument("--band", type=int, default=64, choices=[64, 128])
+    ap.add_argument("--conf-min", type=float, default=0.3)
+    ap.add_argument("--fallback-frac", type=float, default=0.25)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--mixed-distinct", type=int, default=3,
                     help="distinct generated pairs per shape in the mixed batch (reused cyclically)")
@@ -376,6 +482,8 @@ def main():
         return run_mixed(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "learned":
+        return run_learned(args, rank, world)
 
     import numpy as np
     import torch
