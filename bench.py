@@ -372,9 +372,12 @@ def run_learned(args, rank, world):
         return 0
     import multiprocessing as mp
     W_, H_, D_ = 1920, 1080, 256
+    nb = args.learned_batch
     jobs = [(6000 + i, W_, H_, D_) for i in range(args.eval_frames)]
     with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:   # before any GPU call
         frames = pool.map(_gen_street, jobs)
+    if len(frames) % nb:
+        raise SystemExit("--eval-frames must be a multiple of --learned-batch")
     import numpy as np
     import torch
     from paper_2504_05148_gb300 import build as _build
@@ -387,15 +390,17 @@ def run_learned(args, rank, world):
         print(json.dumps({"metric": "learned band", "unavailable": f"no trained weights at {wpath}"}))
         return 0
     net.load(wpath)
-    dl = [torch.from_numpy(f[0][None]).to(dev) for f in frames]
-    dr = [torch.from_numpy(f[1][None]).to(dev) for f in frames]
-    dli = [torch.from_numpy(f[2][None]).to(dev) for f in frames]
+    groups = [list(range(g, g + nb)) for g in range(0, len(frames), nb)]
+    stack = lambda k, idx: torch.from_numpy(np.stack([frames[i][k] for i in idx])).to(dev)
+    dl = [stack(0, g) for g in groups]
+    dr = [stack(1, g) for g in groups]
+    dli = [stack(2, g) for g in groups]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    plain = sgmf.Context(W_, H_, D_)
+    plain = sgmf.Context(W_, H_, D_, max_batch=nb)
     learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
-                                 fallback_frac=args.fallback_frac)
-    outp = [torch.empty((1, H_, W_), dtype=torch.int16, device=dev) for _ in frames]
-    outl = [torch.empty((1, H_, W_), dtype=torch.int16, device=dev) for _ in frames]
+                                 fallback_frac=args.fallback_frac, max_batch=nb)
+    outp = [torch.empty((nb, H_, W_), dtype=torch.int16, device=dev) for _ in groups]
+    outl = [torch.empty((nb, H_, W_), dtype=torch.int16, device=dev) for _ in groups]
 
     def timed(fn, i):
         flush.zero_()
@@ -408,9 +413,9 @@ def run_learned(args, rank, world):
         b.synchronize()
         return a.elapsed_time(b)
 
-    run_p = lambda i: plain.compute(dl[i][0], dr[i][0], dli[i][0], outp[i][0])
+    run_p = lambda i: plain.compute(dl[i], dr[i], dli[i], outp[i])
     run_l = lambda i: learned.compute(dl[i], dr[i], dli[i], outl[i])
-    for i in range(min(len(frames), max(args.warmup, 1))):
+    for i in range(len(groups)):
         run_p(i)
         run_l(i)
     torch.cuda.synchronize()
@@ -419,32 +424,47 @@ def run_learned(args, rank, world):
     clocks.start()
     tp, tl = [], []
     for _ in range(args.steps_learned):
-        for i in range(len(frames)):
+        for i in range(len(groups)):
             tp.append(timed(run_p, i))
             tl.append(timed(run_l, i))
     clk = clocks.stop()
+    # per-stage split of the learned path and per-kernel times of both (one more profiled call each)
+    plain.set_profiling(True)
+    learned.banded.set_profiling(True)
+    learned.marks = []
+    timed(run_p, 0)
+    timed(run_l, 0)
+    ev = learned.marks
+    learned.marks = None
+    stages = {ev[k][0]: ev[k - 1][1].elapsed_time(ev[k][1]) for k in range(1, len(ev))}
+    kp = {k: round(v, 4) for k, v in plain.kernel_times()}
+    kl = {k: round(v, 4) for k, v in learned.banded.kernel_times()}
+    plain.set_profiling(False)
+    learned.banded.set_profiling(False)
     plain.sync()
     learned.sync()
-    dis = [bandnet.disagreement(outl[i].cpu().numpy()[0], outp[i].cpu().numpy()[0]) for i in range(len(frames))]
-    whd = W_ * H_ * D_
+    dis = [bandnet.disagreement(outl[g][j].cpu().numpy(), outp[g][j].cpu().numpy())
+           for g in range(len(groups)) for j in range(nb)]
+    whd = W_ * H_ * D_ * nb
     vp, vl = whd / (np.mean(tp) * 1e-3), whd / (np.mean(tl) * 1e-3)
     st = learned.stats
     line = {
         "metric": "W*H*D/s at 1920x1080 D=256, learned band vs plain full range", "value": vl, "unit": UNIT,
-        "n_gpus": 1, "steps": len(tl), "warmup": args.warmup, "ms_per_step": float(np.mean(tl)),
+        "n_gpus": 1, "steps": len(tl), "warmup": 1, "ms_per_step": float(np.mean(tl)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16 (SGM), bf16 (network)",
         "data": "synthetic",
-        "learned": {"W*H*D/s": vl, "ms_per_frame": float(np.mean(tl)), "band": args.band,
+        "learned": {"W*H*D/s": vl, "ms_per_frame": float(np.mean(tl)) / nb, "band": args.band,
                     "speedup_vs_plain": vl / vp, "px_off_by_more_than_1": float(np.mean(dis)),
                     "px_off_by_more_than_1_max_frame": float(np.max(dis)),
                     "fallback_rate": st["fallback_frames"] / max(st["frames"], 1),
                     "uncertain_tile_fraction": st["uncertain_tiles"] / max(st["tiles"], 1),
-                    "conf_min": args.conf_min, "fallback_frac": args.fallback_frac},
-        "plain": {"W*H*D/s": vp, "ms_per_frame": float(np.mean(tp))},
-        "config": {"workload": "street_1920x1080_d256_unseen_seeds", "frames": len(frames),
+                    "conf_min": args.conf_min, "fallback_frac": args.fallback_frac,
+                    "stage_ms": {k: round(v, 4) for k, v in stages.items()}, "kernel_ms": kl},
+        "plain": {"W*H*D/s": vp, "ms_per_frame": float(np.mean(tp)) / nb, "kernel_ms": kp},
+        "config": {"workload": "street_1920x1080_d256_unseen_seeds", "frames": len(frames), "batch": nb,
                    "network": "6 x conv3x3, 32 ch, quarter resolution, bf16/f32 on tcgen05",
-                   "weights": os.path.relpath(wpath, ROOT), "batch": 1,
-                   "l2": "flushed by a 512 MiB write before every frame"},
+                   "weights": os.path.relpath(wpath, ROOT),
+                   "l2": "flushed by a 512 MiB write before every call"},
         "roofline": None, "cpu_baseline": None,
         "e2e": None, "gpu_launches": None, "clocks": clk,
     }
@@ -464,7 +484,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve", "learned"])
-    ap.add_argument("--eval-frames", type=int, default=6)
+    ap.add_argument("--eval-frames", type=int, default=8)
+    ap.add_argument("--learned-batch", type=int, default=1)
     ap.add_argument("--steps-learned", type=int, default=3)
     ap.add_argument("--band", type=int, default=64, choices=[64, 128])
     ap.add_argument("--conf-min", type=float, default=0.3)

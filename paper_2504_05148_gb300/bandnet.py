@@ -225,6 +225,30 @@ def train(net: BandNet, x_all, lohi_all, counts, steps: int, batch: int = 16, lr
     return hist
 
 
+def evaluate(net: BandNet, x_all, lohi_all, counts, batch: int = 16, D: int = 128) -> float:
+    """Mean band loss over the whole set (labelled pixels weighted equally)."""
+    import torch
+    dev = torch.device("cuda")
+    N, H4, W4, _ = x_all.shape
+    out = torch.empty((batch, H4, W4, C), dtype=torch.float32, device=dev)
+    grad = torch.empty((batch, H4, W4, C), dtype=torch.int16, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    total, labelled = 0.0, 0
+    for i in range(0, N, batch):
+        nb = min(batch, N - i)
+        c = int(counts[i:i + nb].sum())
+        cnt.fill_(c)
+        loss.zero_()
+        _, o = net.forward(x_all[i:i + nb], nb, H4, W4, out=out[:nb])
+        S.sgmf_bn_loss(nb * H4 * W4, D, o.data_ptr(), lohi_all[i:i + nb].data_ptr(), cnt.data_ptr(),
+                       grad.data_ptr(), loss.data_ptr())
+        total += float(loss.item()) * c
+        labelled += c
+    net.check()
+    return total / max(labelled, 1)
+
+
 # ---- inference ------------------------------------------------------------------------
 
 class LearnedSGM:
@@ -250,13 +274,24 @@ class LearnedSGM:
         self.lo = torch.empty((n, self.th, self.tw), dtype=torch.int16, device=dev)
         self.unc = torch.zeros(1, dtype=torch.int32, device=dev)
         self.stats = {"frames": 0, "fallback_frames": 0, "uncertain_tiles": 0, "tiles": 0}
+        self.marks = None          # set to a list to receive (name, cuda event) pairs per compute
 
     def compute(self, left, right, lidar, out):
         """left/right uint8, lidar float32, out int16: (n, H, W) CUDA tensors.
         Returns True when the batch fell back to the plain method."""
+        import torch
         n = left.shape[0] if left.dim() == 3 else 1
+
+        def mark(name):
+            if self.marks is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                self.marks.append((name, e))
+
+        mark("start")
         S.sgmf_compute_front(self.banded.handle, n, left.data_ptr(), right.data_ptr(),
                              lidar.data_ptr() if lidar is not None else None)
+        mark("front")
         S.sgmf_bn_input(n, self.W, self.H, self.D, left.data_ptr(), S.sgmf_prior_device(self.banded.handle),
                         self.x.data_ptr())
         self.acts[0] = self.x
@@ -268,6 +303,7 @@ class LearnedSGM:
         self.unc.zero_()
         S.sgmf_bn_tiles(n, self.W, self.H, self.D, self.band, self.conf_min, self.out.data_ptr(), self.lo.data_ptr(),
                         self.unc.data_ptr())
+        mark("network")
         unc = int(self.unc.item())     # waits for the proposal
         tiles = n * self.th * self.tw
         self.stats["frames"] += n
@@ -278,6 +314,7 @@ class LearnedSGM:
             self.plain.compute(left, right, lidar, out)
             return True
         S.sgmf_compute_banded_back(self.banded.handle, n, self.lo.data_ptr(), out.data_ptr())
+        mark("back")
         return False
 
     def sync(self):

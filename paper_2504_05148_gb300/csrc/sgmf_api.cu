@@ -637,6 +637,7 @@ extern "C" sgmf_status sgmf_compute_front(sgmf_ctx *c, int n, const uint8_t *lef
     mark(c, "semidense");
     LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
   }
+  mark(c, "between_halves");   // the caller's band proposal runs until the back half starts
   c->front_n = n;
   return SGMF_OK;
 }

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "sgmf.h"
@@ -97,7 +98,6 @@ constexpr uint32_t idesc_bf16(int M, int N) {
 constexpr int kBnC = 32;               // channels
 constexpr int kBnK = 9 * kBnC;         // 288
 constexpr int kBnKChunks = kBnK / 8;   // 36 core-matrix columns
-constexpr int kBnA = 128 * kBnK * 2;   // 73728 bytes: the A image of a forward tile
 constexpr int kBnB = kBnC * kBnK * 2;  // 18432 bytes: the packed weights
 
 // byte offset of element (row, k) in a K-major core-matrix image with kc core columns
@@ -137,12 +137,26 @@ struct BnConvArgs {
   int *err;
 };
 
-__global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvArgs a) {
+// One CTA walks `tiles` tiles of 128 consecutive output pixels of one image
+// row.  The three input rows of a tile are staged once, split into the four
+// 8-channel chunks: Xs[ky][chunk][130 pixels][8 channels] (16 bytes per pixel
+// and chunk).  For tap (ky, kx) and channels 16h .. 16h + 15 the A operand is
+// then the staged rows themselves, shifted by kx pixels: its core matrices
+// (8 pixels x 16 bytes) are contiguous 128-byte blocks, the next 8 rows 128
+// bytes further (stride byte offset) and the second chunk one chunk plane
+// further (leading byte offset).  No im2col copy: 18 MMAs read the same
+// ~25 KB of staged input through different descriptor start addresses.
+constexpr int kCvM = 128, kCvPix = kCvM + 2;           // output pixels, staged pixels per row
+constexpr int kCvPlane = kCvPix * 16;                  // bytes of one chunk plane (2080)
+constexpr int kCvX = 3 * 4 * kCvPlane;                 // 24960 bytes of staged input
+constexpr int kCvSmem = kCvX + kBnB + 16;
+
+__global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvArgs a, int tiles) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t *As = sm;
-  uint8_t *Bs = sm + kBnA;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kBnA + kBnB);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + kBnA + kBnB + 8);
+  uint8_t *Xs = sm;
+  uint8_t *Bs = sm + kCvX;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kCvX + kBnB);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + kCvX + kBnB + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     tmem_alloc(slot, 32);
@@ -153,54 +167,65 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
     mbar_fence_init();
   }
   for (int i = tid; i < kBnB / 16; i += 128) reinterpret_cast<uint4 *>(Bs)[i] = a.packed[i];
-  const long long P = (long long)a.n * a.h * a.w;
-  const long long p = (long long)blockIdx.x * 128 + tid;
-  const bool live = p < P;
-  int img = 0, py = 0, px = 0;
-  if (live) {
-    img = (int)(p / ((long long)a.h * a.w));
-    const int r = (int)(p % ((long long)a.h * a.w));
-    py = r / a.w;
-    px = r % a.w;
-  }
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-    const bool in = live && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-    const long long q = in ? ((long long)img * a.h + yy) * a.w + xx : 0;   // no address outside the tensor
-    const uint4 *src = reinterpret_cast<const uint4 *>(a.x + q * kBnC);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint4 v = in ? src[j] : make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4 *>(As + cm_off(tid, tap * kBnC + 8 * j, kBnKChunks)) = v;
-    }
-  }
-  fence_async_smem();
+  const int tpr = (a.w + kCvM - 1) / kCvM;                   // tiles per image row
+  const long long ntile = (long long)a.n * a.h * tpr;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
-  if (tid == 0) {
-    const uint32_t idesc = idesc_bf16(128, 32);
-    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+  const uint32_t idesc = idesc_bf16(128, 32);
+  bool ok = true;
+  int phase = 0;
+  for (int it = 0; it < tiles && ok; ++it) {
+    const long long tile = (long long)blockIdx.x * tiles + it;
+    if (tile >= ntile) break;                                // CTA-uniform
+    const int tx = (int)(tile % tpr);
+    const long long row = tile / tpr;                        // img * h + y
+    const int y = (int)(row % a.h);
+    const long long img = row / a.h;
+    const int x0 = tx * kCvM;
+    // stage rows y-1, y, y+1, pixels x0-1 .. x0+128, as chunk planes
+    for (int i = tid; i < 3 * kCvPix * 4; i += 128) {
+      const int j = i & 3, px = (i >> 2) % kCvPix, ky = (i >> 2) / kCvPix;
+      const int yy = y + ky - 1, xx = x0 - 1 + px;
+      const bool in = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+      const long long q = in ? (img * a.h + yy) * a.w + xx : 0;
+      const uint4 v = in ? reinterpret_cast<const uint4 *>(a.x + q * kBnC)[j] : make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4 *>(Xs + (ky * 4 + j) * kCvPlane + px * 16) = v;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t x_0 = smem_u32(Xs), b0 = smem_u32(Bs);
 #pragma unroll 1
-    for (int s = 0; s < kBnK / 16; ++s)
-      umma_bf16(tmem, sdesc(a0 + s * 256, 128, kBnKChunks * 128), sdesc(b0 + s * 256, 128, kBnKChunks * 128),
-                idesc, s > 0 ? 1u : 0u);
-    umma_commit(bar);
-  }
-  __syncwarp();
-  bool ok = mbar_wait_bounded(bar, 0, kWaitLimit);
-  if (!__syncthreads_and(ok)) {
-    if (tid == 0) set_error(a.err, kErrTimeout);
-    mbar_wait_bounded(bar, 0, kWaitLimit);   // let the MMAs in flight finish before freeing their memory
-    ok = false;
-  }
-  tc_fence_after();
-  if (ok) {
+      for (int t = 0; t < 9; ++t) {
+        const int ky = t / 3, kx = t % 3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t as = x_0 + (ky * 4 + 2 * h) * kCvPlane + kx * 16;
+          umma_bf16(tmem, sdesc(as, kCvPlane, 128), sdesc(b0 + (t * 2 + h) * 256, 128, kBnKChunks * 128), idesc,
+                    (t > 0 || h > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(bar);
+    }
+    __syncwarp();
+    const bool w_ok = mbar_wait_bounded(bar, (uint32_t)(phase & 1), kWaitLimit);
+    ++phase;
+    if (!__syncthreads_and(w_ok)) {
+      if (tid == 0) set_error(a.err, kErrTimeout);
+      mbar_wait_bounded(bar, (uint32_t)((phase - 1) & 1), kWaitLimit);   // MMAs in flight finish first
+      ok = false;
+      break;
+    }
+    tc_fence_after();
     float v[32];
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-    if (live) {
+    const int x = x0 + tid;
+    if (x < a.w) {
+      const long long p = row * a.w + x;
       if (a.bias) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) v[c] += a.bias[c];
@@ -241,6 +266,10 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
         }
       }
     }
+    // the accumulator and the staged input are reused by the next tile
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
   tc_fence_before();
   __syncthreads();
@@ -563,18 +592,11 @@ extern "C" sgmf_status sgmf_bn_pack(const uint16_t *w, uint16_t *packed_fwd, uin
 extern "C" sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, const uint16_t *packed, const float *bias,
                                     int relu, const uint16_t *mask, uint16_t *y, float *yf, int *err, void *stream) {
   if (n < 1 || h < 1 || w < 1 || !x || !packed || !err || (!y && !yf)) return SGMF_ERR_ARG;
-  static bool attr[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const int smem = kBnA + kBnB + 16;
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_bn_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_conv attribute");
-    attr[dev] = true;
-  }
+  const long long ntile = (long long)n * h * ((w + kCvM - 1) / kCvM);
+  // about four CTAs per SM, each walking consecutive tiles with its weights staged once
+  const int tiles = (int)std::max<long long>(1, std::min<long long>(8, ntile / (4 * 152)));
   BnConvArgs a{n, h, w, x, reinterpret_cast<const uint4 *>(packed), bias, relu, mask, y, yf, err};
-  const long long P = (long long)n * h * w;
-  k_bn_conv<<<(unsigned)((P + 127) / 128), 128, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  k_bn_conv<<<(unsigned)((ntile + tiles - 1) / tiles), 128, kCvSmem, static_cast<cudaStream_t>(stream)>>>(a, tiles);
   return bn_launch(cudaGetLastError(), "sgmf_bn_conv");
 }
 

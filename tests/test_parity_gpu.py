@@ -129,6 +129,7 @@ PARAM_CASES = {
     "zero_pen": S.Params(p1=0, p2=0),
     "ts9": S.Params(ts=9),
     "wide_windows": S.Params(rs=15, rc=40, tc=5),
+    "huge_windows": S.Params(rs=50, rc=60, tc=3),          # the separable box-OR (radius > 48)
     "zero_windows": S.Params(rs=0, rc=0, tc=0),
     "lr2": S.Params(lr_max_diff=2),
     "full_census_big_p2": S.Params(census=S.SGMF_CENSUS_9X7, p2=1000, q2=200),
