@@ -396,6 +396,19 @@ def run_learned(args, rank, world):
     dr = [stack(1, g) for g in groups]
     dli = [stack(2, g) for g in groups]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    if args.no_plain:
+        # the learned path alone (a small device footprint, for profiling)
+        learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
+                                     fallback_frac=args.fallback_frac, max_batch=nb)
+        out = torch.empty((nb, H_, W_), dtype=torch.int16, device=dev)
+        for _ in range(max(args.steps_learned, 1) + 1):
+            for i in range(len(groups)):
+                learned.compute(dl[i], dr[i], dli[i], out)
+        learned.sync()
+        print(json.dumps({"metric": "learned band path only (profiling run)", "frames": len(frames),
+                          "stats": learned.stats}), flush=True)
+        learned.close()
+        return 0
     plain = sgmf.Context(W_, H_, D_, max_batch=nb)
     learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
                                  fallback_frac=args.fallback_frac, max_batch=nb)
@@ -486,6 +499,7 @@ def main():
     ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve", "learned"])
     ap.add_argument("--eval-frames", type=int, default=8)
     ap.add_argument("--learned-batch", type=int, default=1)
+    ap.add_argument("--no-plain", action="store_true", help="learned workload: skip the plain comparison")
     ap.add_argument("--steps-learned", type=int, default=3)
     ap.add_argument("--band", type=int, default=64, choices=[64, 128])
     ap.add_argument("--conf-min", type=float, default=0.3)
