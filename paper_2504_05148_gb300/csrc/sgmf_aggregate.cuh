@@ -306,7 +306,7 @@ template <int CPL, bool S8, int NWARP>
 struct LineCfg {
   static constexpr int Dp = 16 * CPL;
   static constexpr int K = CPL <= 8 ? 8 : 4;   // rows per stage
-  static constexpr int S = 3;                  // stages per warp
+  static constexpr int S = 2;                  // stages per warp
   static constexpr int SB = S8 ? 1 : 2;        // spill bytes per cell
   static constexpr int kCost = K * 2 * Dp;     // [row][line of the warp][Dp]
   static constexpr int kSpillLine = K * Dp * SB;
@@ -551,7 +551,7 @@ template <int CPL, bool S8>
 struct RowCfg {
   static constexpr int Dp = 16 * CPL;
   static constexpr int K = CPL <= 8 ? 4 : 2;    // walk steps per stage
-  static constexpr int S = 3;
+  static constexpr int S = 2;
   static constexpr int SB = S8 ? 1 : 2;
   static constexpr int kCost = K * Dp;
   static constexpr int kSpill = K * Dp * SB;
