@@ -206,7 +206,7 @@ size_t sgmf_device_bytes(const sgmf_ctx *c);
 
 /* ---- Banded mode (no counterpart in the paper) ---------------------------
  * The method restricted to a disparity band per pixel: pixel p keeps the
- * disparities [lo_p, lo_p + band); lo_p is constant on 16 x 16 pixel tiles.
+ * disparities [lo_p, lo_p + band); lo_p is constant on 8 x 8 pixel tiles.
  * Eq. 2 runs on the bands (a term whose disparity is outside the previous
  * pixel's band is left out; m is the min over that band), d* is the argmin
  * over the pixel's band, d'(x') the argmin over the cells (x' + d, d) that
@@ -220,7 +220,7 @@ size_t sgmf_device_bytes(const sgmf_ctx *c);
 sgmf_status sgmf_create_banded(int width, int height, int max_disp, int band, int max_batch, sgmf_ctx **out);
 
 /* sgmf_compute_batch with band starts: band_lo is a DEVICE int16 array
- * [n][ceil(H / 16)][ceil(W / 16)] (tile rows, then tile columns); values are
+ * [n][ceil(H / 8)][ceil(W / 8)] (tile rows, then tile columns); values are
  * clamped to [0, max_disp - band].  subpixel must be 0. */
 sgmf_status sgmf_compute_banded(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
                                 const float *lidar, const int16_t *band_lo, int16_t *out);
@@ -294,9 +294,9 @@ sgmf_status sgmf_bn_adam(int count, float *w, float *m, float *v, const float *g
                          float eps, int step, uint16_t *w_bf16, void *stream);
 
 /* Band starts from the network output out (f32 [n][H4][W4][32]) for a
- * banded context of width `band`: per 16 x 16 tile the union [lo, hi] of the
+ * banded context of width `band`: per 8 x 8 tile the union [lo, hi] of the
  * pixels' bands [c - w, c + w], start round((lo + hi) / 2) - band / 2 clamped
- * to [0, max_disp - band] into lo_tiles int16 [n][ceil(H/16)][ceil(W/16)];
+ * to [0, max_disp - band] into lo_tiles int16 [n][ceil(H/8)][ceil(W/8)];
  * *uncertain += tiles whose smallest confidence is below conf_min or whose
  * union is wider than the band. */
 sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp, int band, float conf_min, const float *out,

@@ -9,7 +9,7 @@ calls.
 
 Inference (LearnedSGM): the banded context's front half (ingest, census,
 semidensification) gives d-hat; the network turns it into one band start
-per 16 x 16 tile; if more than `fallback_frac` of the tiles are uncertain
+per 8 x 8 tile; if more than `fallback_frac` of the tiles are uncertain
 (low confidence or a union of pixel bands wider than the band), the frame
 falls back to the plain full-range method, else the banded back half
 finishes it.
@@ -265,7 +265,7 @@ class LearnedSGM:
         self.plain = S.Context(W, H, D, params, max_batch=max_batch)
         dev = torch.device("cuda")
         self.H4, self.W4 = _q(4, H), _q(4, W)
-        self.th, self.tw = _q(16, H), _q(16, W)
+        self.th, self.tw = _q(S.BAND_TILE, H), _q(S.BAND_TILE, W)
         n = max_batch
         self.x = torch.empty((n, self.H4, self.W4, C), dtype=torch.int16, device=dev)
         self.acts = [None] + [torch.empty((n, self.H4, self.W4, C), dtype=torch.int16, device=dev)

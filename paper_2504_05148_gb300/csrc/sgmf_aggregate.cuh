@@ -222,7 +222,7 @@ __device__ __forceinline__ void pad_bytes(int D, int lig, uint32_t (&z)[CPL / 4]
 
 // ---- disparity bands (banded mode, not in the paper) -----------------------------
 // In banded mode lane cell j of pixel p stands for disparity lo_p + j, with
-// lo_p constant on 16 x 16 pixel tiles.  A group walking its line tracks the
+// lo_p constant on 8 x 8 pixel tiles.  A group walking its line tracks the
 // tile of each step; where the band start changes by delta, the previous
 // pixel's path costs are re-indexed: cell j takes old cell j + delta, and the
 // cells that have no old counterpart become absent (kInf, above every real
@@ -263,7 +263,7 @@ template <int CPL>
 __device__ __forceinline__ void band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig) {
   int delta = 0;
   if (active) {
-    const int t = (bs.y >> 4) * bs.tw + (bs.x >> 4);
+    const int t = (bs.y >> kBandTileLog) * bs.tw + (bs.x >> kBandTileLog);
     if (t != bs.tile) {
       bs.tile = t;
       const int nlo = bs.lo[t];
@@ -298,7 +298,7 @@ struct LineArgs {
   void *spill;            // [3][W][H][Dp] elements
   int *err;
   StepConsts sc;
-  const int16_t *lo;      // banded mode: band starts per 16 x 16 tile, [frame][th][tw]
+  const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]
   int tw, th;
 };
 
@@ -542,7 +542,7 @@ struct RowArgs {
   uint16_t *dbg_sum;
   int *err;
   StepConsts sc;
-  const int16_t *lo;      // banded mode: band starts per 16 x 16 tile, [frame][th][tw]
+  const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]
   int tw, th;
   uint16_t *sum;          // banded mode: S of every frame, [frame][H][W][Dp]
 };

@@ -211,8 +211,8 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   if (band) {                // lanes and volumes hold the band only
     k.Dp = band;
     k.DPL = band / 32;
-    k.tw = (width + 15) / 16;
-    k.th = (height + 15) / 16;
+    k.tw = (width + kBandTile - 1) / kBandTile;
+    k.th = (height + kBandTile - 1) / kBandTile;
   }
   k.pitch = (width + 15) / 16 * 16;
   k.line_warps = 4;

@@ -1,6 +1,6 @@
 // sgmf_band.cu -- kernels of the banded mode (not in the paper): the method
 // restricted to a disparity band [lo_p, lo_p + B) per pixel, lo_p constant on
-// 16 x 16 pixel tiles.  Ingest, census, semidensification and the check are
+// kBandTile x kBandTile pixel tiles.  Ingest, census, semidensification and the check are
 // the plain kernels; the cost, the aggregation (sgmf_aggregate.cuh, BANDED
 // variants) and the WTA work on the bands.
 #include <cstdint>
@@ -23,7 +23,7 @@ cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const 
 }
 
 // Banded cost: cell j of pixel p holds C-bar(p, lo_p + j) (Eq. 4, the plain
-// rules).  A CTA handles 64 pixels (four tiles) of one row; the right-census
+// rules).  A CTA handles 64 pixels (several tiles) of one row; the right-census
 // window covering all their bands is staged in shared memory and the lanes
 // of a warp walk the cells of one pixel.
 constexpr int kBandCostPx = 64;
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
   __shared__ CT cr_s[kBandCostPx + B + kMaxDisp];
   __shared__ CT cl_s[kBandCostPx];
   __shared__ int pd_s[kBandCostPx];
-  __shared__ int lo_s[kBandCostPx / 16];
+  __shared__ int lo_s[kBandCostPx / kBandTile];
   __shared__ uint8_t tab_s[4 * 64];
   __shared__ __align__(16) uint8_t out_s[kBandCostPx * B];
   const Buffers b = frame_view(k, b0, blockIdx.z);
@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
   const int npx = min(kBandCostPx, W - x0);
-  const int ntile = (npx + 15) / 16;
-  if (threadIdx.x < kBandCostPx / 16)
-    lo_s[threadIdx.x] = threadIdx.x < ntile ? b.band_lo[(y >> 4) * k.tw + (x0 >> 4) + threadIdx.x] : 0;
+  const int ntile = (npx + kBandTile - 1) / kBandTile;
+  if (threadIdx.x < kBandCostPx / kBandTile)
+    lo_s[threadIdx.x] =
+        threadIdx.x < ntile ? b.band_lo[(y >> kBandTileLog) * k.tw + (x0 >> kBandTileLog) + threadIdx.x] : 0;
   for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
   int lo_min = lo_s[0], lo_max = lo_s[0];
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
     const int x = x0 + px;
     const CT c = cl_s[px];
     const int pd = pd_s[px];
-    const int lo = lo_s[px >> 4];
+    const int lo = lo_s[px >> kBandTileLog];
 #pragma unroll
     for (int m = 0; m < B / 32; ++m) {
       const int j = lane + 32 * m, d = lo + j;
@@ -127,9 +128,9 @@ __global__ void __launch_bounds__(256) k_wta_banded(KParams k, Buffers b0) {
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int CL = B / 32;   // cells per lane: 2 or 4
-  const int16_t *lo_row = b.band_lo + (size_t)(y >> 4) * k.tw;
+  const int16_t *lo_row = b.band_lo + (size_t)(y >> kBandTileLog) * k.tw;
   for (int x = warp; x < W; x += 8) {
-    const int lo = lo_row[x >> 4];
+    const int lo = lo_row[x >> kBandTileLog];
     const uint16_t *sp = b.band_sum + ((size_t)y * W + x) * B + lane * CL;
     uint32_t v[CL];
     if constexpr (CL == 2) {

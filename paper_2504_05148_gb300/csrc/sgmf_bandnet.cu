@@ -540,23 +540,25 @@ __global__ void k_bn_adam(int count, float *__restrict__ w, float *__restrict__ 
   if (wb) wb[i] = f2bf(wi);
 }
 
-// ---- network output -> band starts per 16 x 16 tile ----------------------------------------
-// For each tile (4 x 4 quarter pixels): the union [lo_u, hi_u] of the pixels'
+// ---- network output -> band starts per tile ----------------------------------------------
+// For each tile (kBandTile / 4 quarter pixels a side): the union [lo_u, hi_u] of the pixels'
 // bands [c - w, c + w]; band start lo = round((lo_u + hi_u) / 2) - B / 2,
 // clamped to [0, D - B].  A tile is uncertain when the smallest confidence in
 // it is below conf_min or the union is wider than B; *uncertain counts them.
 __global__ void k_bn_tiles(int n, int W, int H, int D, int B, float conf_min, const float *__restrict__ out,
                            int16_t *__restrict__ lo_tiles, int *uncertain) {
-  const int H4 = (H + 3) / 4, W4 = (W + 3) / 4, th = (H + 15) / 16, tw = (W + 15) / 16;
+  constexpr int Q = kBandTile / 4;   // quarter pixels per tile side
+  const int H4 = (H + 3) / 4, W4 = (W + 3) / 4, th = (H + kBandTile - 1) / kBandTile,
+            tw = (W + kBandTile - 1) / kBandTile;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)n * th * tw) return;
   const int f = (int)(i / ((long long)th * tw));
   const int r = (int)(i % ((long long)th * tw));
   const int ty = r / tw, tx = r % tw;
   float lo_u = 1e30f, hi_u = -1e30f, qmin = 1.0f;
-  for (int dy = 0; dy < 4; ++dy)
-    for (int dx = 0; dx < 4; ++dx) {
-      const int qy = 4 * ty + dy, qx = 4 * tx + dx;
+  for (int dy = 0; dy < Q; ++dy)
+    for (int dx = 0; dx < Q; ++dx) {
+      const int qy = Q * ty + dy, qx = Q * tx + dx;
       if (qy >= H4 || qx >= W4) continue;
       const float *o = out + (((long long)f * H4 + qy) * W4 + qx) * kBnC;
       const float c = D * o[0];
@@ -660,7 +662,7 @@ extern "C" sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp,
                                      const float *out, int16_t *lo_tiles, int *uncertain, void *stream) {
   if (n < 1 || width < 1 || height < 1 || band < 1 || band > max_disp || !out || !lo_tiles || !uncertain)
     return SGMF_ERR_ARG;
-  const long long NT = (long long)n * ((height + 15) / 16) * ((width + 15) / 16);
+  const long long NT = (long long)n * ((height + kBandTile - 1) / kBandTile) * ((width + kBandTile - 1) / kBandTile);
   k_bn_tiles<<<(unsigned)((NT + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       n, width, height, max_disp, band, conf_min, out, lo_tiles, uncertain);
   return bn_launch(cudaGetLastError(), "sgmf_bn_tiles");

@@ -23,6 +23,8 @@ namespace sgmf {
 
 constexpr int kMaxDisp = 256;
 constexpr int kMaxDim = 8192;
+// banded mode: the band start is constant on kBandTile x kBandTile pixel tiles
+constexpr int kBandTileLog = 3, kBandTile = 1 << kBandTileLog;
 constexpr uint32_t kInf = 0x4000u;          // u16 lane value above every real path cost
 constexpr uint32_t kInf2 = kInf | (kInf << 16);
 
@@ -38,7 +40,7 @@ struct KParams {
   int nbits;
   int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA
   int band;                   // banded mode: band width B (= Dp); 0 = the plain method
-  int tw, th;                 // banded mode: 16 x 16 band tiles per row / column                  // census bits (31 or 62)
+  int tw, th;                 // banded mode: band tiles per row / column                  // census bits (31 or 62)
 };
 
 struct Buffers {   // base pointers of frame 0

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsgmf.so")
 SGMF_OK, SGMF_ERR_ARG, SGMF_ERR_PARAM, SGMF_ERR_SHAPE, SGMF_ERR_OOM, SGMF_ERR_CUDA, SGMF_ERR_TIMEOUT = range(7)
 SGMF_CENSUS_CS9X7, SGMF_CENSUS_9X7 = 0, 1
 SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 0, 1, 2, 3
+BAND_TILE = 8   # banded mode: pixels per side of a band tile (include/sgmf.h)
 (SGMF_STAGE_DBAR, SGMF_STAGE_CENSUS_L, SGMF_STAGE_CENSUS_R, SGMF_STAGE_DHAT, SGMF_STAGE_COST,
  SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME, SGMF_STAGE_DSUB) = range(9)
 
@@ -311,7 +312,7 @@ def sgmf_create_banded(width: int, height: int, max_disp: int, band: int, max_ba
 
 
 def sgmf_compute_banded(ctx: int, n: int, left: int, right: int, lidar: int | None, band_lo: int, out: int) -> None:
-    """Device pointers; band_lo int16 [n][ceil(H/16)][ceil(W/16)]."""
+    """Device pointers; band_lo int16 [n][ceil(H/8)][ceil(W/8)]."""
     _check(lib().sgmf_compute_banded(ctx, n, left, right, lidar or None, band_lo, out), ctx)
 
 
@@ -531,11 +532,11 @@ class Context:
         sgmf_compute_batch(self.handle, n, left.data_ptr(), right.data_ptr(), lp, out.data_ptr())
 
     def compute_banded(self, left, right, lidar, band_lo, out) -> None:
-        """torch CUDA tensors as in compute(), plus band_lo: int16 (n, ceil(H/16), ceil(W/16))
+        """torch CUDA tensors as in compute(), plus band_lo: int16 (n, ceil(H/8), ceil(W/8))
         (or without the frame axis for one frame)."""
         shape = tuple(left.shape)
         n = 1 if len(shape) == 2 else shape[0]
-        th, tw = (self.H + 15) // 16, (self.W + 15) // 16
+        th, tw = (self.H + BAND_TILE - 1) // BAND_TILE, (self.W + BAND_TILE - 1) // BAND_TILE
         if str(band_lo.dtype) != "torch.int16" or not band_lo.is_cuda or not band_lo.is_contiguous() \
                 or band_lo.numel() != n * th * tw:
             raise ValueError(f"band_lo must be a contiguous CUDA int16 tensor of {n} x {th} x {tw}")

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _tiles(W, H):
-    return (H + 15) // 16, (W + 15) // 16
+    return (H + S.BAND_TILE - 1) // S.BAND_TILE, (W + S.BAND_TILE - 1) // S.BAND_TILE
 
 
 def _gpu(scene, B, lo_tiles, params=None, lidar=True):
@@ -37,7 +37,7 @@ def _check(scene, B, lo_tiles, params=None, lidar=True):
     params = params or S.Params()
     lo_c = np.clip(lo_tiles, 0, scene.D - B).astype(np.int16)
     g = _gpu(scene, B, lo_tiles, params, lidar)
-    lo = oracle.expand_tiles(lo_c, scene.W, scene.H)
+    lo = oracle.expand_tiles(lo_c, scene.W, scene.H, S.BAND_TILE)
     o = oracle.compute_banded(scene.left, scene.right, scene.lidar if lidar else None, scene.D, B, lo,
                               oracle.Params(**vars(params)), volumes=True)
     plain = oracle.compute(scene.left, scene.right, scene.lidar if lidar else None, scene.D,
@@ -69,9 +69,10 @@ def test_smooth_bands_from_the_truth(gpu):
     B = 64
     th, tw = _tiles(s.W, s.H)
     lo = np.zeros((th, tw), np.int64)
+    T = S.BAND_TILE
     for ty in range(th):
         for tx in range(tw):
-            blk = s.truth[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16]
+            blk = s.truth[T * ty:T * ty + T, T * tx:T * tx + T]
             lo[ty, tx] = int(np.median(blk)) - B // 2
     g, o = _check(s, B, lo)
     assert (g["out"] >= 0).mean() > 0.5
@@ -113,7 +114,8 @@ def test_batch(gpu):
     finally:
         ctx.close()
     for i, s in enumerate(scs):
-        o = oracle.compute_banded(s.left, s.right, s.lidar, s.D, 64, oracle.expand_tiles(los[i], 120, 50))
+        o = oracle.compute_banded(s.left, s.right, s.lidar, s.D, 64,
+                                  oracle.expand_tiles(los[i], 120, 50, S.BAND_TILE))
         np.testing.assert_array_equal(got[i], o.out, err_msg=f"frame {i}")
 
 

@@ -191,7 +191,8 @@ def test_input_labels_loss_tiles_adam(gpu):
     np.testing.assert_allclose(gg, N.bf16_round(rg), rtol=2.0 ** -7, atol=1e-9)
     # band starts per tile
     B, qmin = 64, 0.5
-    lo_t = torch.empty((n, (H + 15) // 16, (W + 15) // 16), dtype=torch.int16, device="cuda")
+    T = S.BAND_TILE
+    lo_t = torch.empty((n, (H + T - 1) // T, (W + T - 1) // T), dtype=torch.int16, device="cuda")
     unc = torch.zeros(1, dtype=torch.int32, device="cuda")
     S.sgmf_bn_tiles(n, W, H, D, B, qmin, _dev(out).data_ptr(), lo_t.data_ptr(), unc.data_ptr())
     c, wv, q = N.heads(out.astype(np.float64), D)
@@ -200,7 +201,8 @@ def test_input_labels_loss_tiles_adam(gpu):
     for f in range(n):
         for ty in range(got.shape[1]):
             for tx in range(got.shape[2]):
-                sl = (f, slice(4 * ty, 4 * ty + 4), slice(4 * tx, 4 * tx + 4))
+                Q = T // 4
+                sl = (f, slice(Q * ty, Q * ty + Q), slice(Q * tx, Q * tx + Q))
                 lo_u, hi_u = (c[sl] - wv[sl]).min(), (c[sl] + wv[sl]).max()
                 mid = np.rint(0.5 * (lo_u + hi_u))
                 assert abs(int(got[f, ty, tx]) - int(np.clip(mid - B // 2, 0, D - B))) <= 1

@@ -93,7 +93,7 @@ def test_learned_pipeline_is_the_banded_method(gpu, trained):
     s = scenes.street(910000, 320, 96, 128)
     got, lo_t, fell, _ = _run_learned(net, s, 64)
     assert not fell
-    o = oracle.compute_banded(s.left, s.right, s.lidar, s.D, 64, oracle.expand_tiles(lo_t, s.W, s.H))
+    o = oracle.compute_banded(s.left, s.right, s.lidar, s.D, 64, oracle.expand_tiles(lo_t, s.W, s.H, S.BAND_TILE))
     np.testing.assert_array_equal(got, o.out)
 
 
