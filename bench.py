@@ -170,6 +170,30 @@ def time_oracle(frames, budget_s: float = 12.0, max_frames: int = 8):
             "ms_per_frame": 1e3 * dt / n}
 
 
+def _oracle_frame(args):
+    import oracle
+    left, right, lidar, D_ = args
+    oracle.compute(left, right, lidar, D_, dumps=False)
+    return 0
+
+
+def time_oracle_all_cores(frames, procs: int):
+    """The same oracle on every host core: independent frames in parallel
+    processes (spawned, so no GPU state is inherited); one frame per process."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    jobs = [(frames[i % len(frames)].left, frames[i % len(frames)].right, frames[i % len(frames)].lidar, D)
+            for i in range(procs)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_frame, jobs[:1])           # process start-up outside the timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_frame, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    return {"value": procs * W * H * D / dt, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} full {W}x{H} D={D} frames, one per process on {procs} cores, {dt:.1f} s"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -588,34 +612,84 @@ def main():
     frames_total = args.steps * B * world
     value = frames_total * W * H * D / (total_ms * 1e-3)
 
-    # end to end through the public host-buffer entry point (pinned host memory)
+    # end to end through the public host-buffer entry points (pinned host memory):
+    # two contexts on two streams take alternate steps, so one step's copies
+    # overlap the other's kernels; every step copies its 16 pairs in and its
+    # 16 outputs back
     e2e = None
+    latency = None
     if not args.no_e2e:
         hl = torch.from_numpy(np.stack([f.left for f in frames])).pin_memory().numpy()
         hr = torch.from_numpy(np.stack([f.right for f in frames])).pin_memory().numpy()
         hli = torch.from_numpy(np.stack([f.lidar for f in frames])).pin_memory().numpy()
-        ho = torch.empty((B, H, W), dtype=torch.int16).pin_memory().numpy()
+        ho = [torch.empty((B, H, W), dtype=torch.int16).pin_memory().numpy() for _ in range(2)]
         ctx.set_profiling(False)
-        for _ in range(args.warmup):
-            ctx.compute_host(hl, hr, hli, ho)
+        stream2 = torch.cuda.Stream(device=dev)
+        ctx2 = sgmf.Context(W, H, D, stream=stream2, max_batch=B)
+        if tuning is not None:
+            sgmf.sgmf_set_tuning(ctx2.handle, *tuning)
+        ctxs = [ctx, ctx2]
+
+        def e2e_steps(k):
+            for i in range(k):
+                c = ctxs[i % 2]
+                if i >= 2:
+                    c.sync()
+                sgmf.sgmf_compute_host_batch_async(c.handle, B, hl.ctypes.data, hr.ctypes.data, hli.ctypes.data,
+                                                   ho[i % 2].ctypes.data)
+            for c in ctxs:
+                c.sync()
+
+        e2e_steps(max(args.warmup, 2))
         if pg:
             import torch.distributed as dist
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ctx.compute_host(hl, hr, hli, ho)
+        e2e_steps(args.steps)
         dt = time.perf_counter() - t0
-        te = torch.tensor([dt], dtype=torch.float64, device=dev)
+        # the synchronous entry point, one context, for comparison
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.compute_host(hl, hr, hli, ho[0])
+        dt_sync = time.perf_counter() - t1
+        te = torch.tensor([dt, dt_sync], dtype=torch.float64, device=dev)
         if pg:
             import torch.distributed as dist
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        dt = float(te.item())
+        dt, dt_sync = float(te[0].item()), float(te[1].item())
         e2e = {"value": frames_total * W * H * D / dt, "unit": UNIT,
                "h2d_bytes_per_step": B * (W * H * 2 + W * H * 4), "d2h_bytes_per_step": B * W * H * 2,
-               "frames_per_s": frames_total / dt}
+               "frames_per_s": frames_total / dt, "api": "sgmf_compute_host_batch_async, 2 contexts",
+               "sync_api_frames_per_s": frames_total / dt_sync}
         # the host results must equal the device results
-        if not np.array_equal(ho, dout.cpu().numpy()):
-            raise RuntimeError("host entry point result differs from the device result")
+        for o in ho:
+            if not np.array_equal(o, dout.cpu().numpy()):
+                raise RuntimeError("host entry point result differs from the device result")
+        ctx2.close()
+        # single-frame latency: one pair per call, device-timed and host to host
+        c1 = sgmf.Context(W, H, D, stream=stream, max_batch=1)
+        if tuning is not None:
+            sgmf.sgmf_set_tuning(c1.handle, *tuning)
+        dev_ms, host_ms = [], []
+        o1 = torch.empty((H, W), dtype=torch.int16, device=dev)
+        for it in range(23):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a_ = torch.cuda.Event(enable_timing=True)
+                b_ = torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                c1.compute(dl[0], dr[0], dli[0], o1)
+                b_.record(stream)
+            b_.synchronize()
+            t2 = time.perf_counter()
+            c1.compute_host(hl[0], hr[0], hli[0], ho[0][0])
+            t3 = time.perf_counter()
+            if it >= 3:
+                dev_ms.append(a_.elapsed_time(b_))
+                host_ms.append(1e3 * (t3 - t2))
+        c1.close()
+        latency = {"device_ms_median": statistics.median(dev_ms), "host_to_host_ms_median": statistics.median(host_ms),
+                   "frames": len(dev_ms)}
 
     if rank != 0:
         if pg:
@@ -667,6 +741,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world > 1 and False):
         cpu = time_oracle(frames)
+        cpu["all_cores"] = time_oracle_all_cores(frames, os.cpu_count() or 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -677,6 +752,7 @@ def main():
                    "lidar": "64 beams, ~5% density", "parallelism": f"replicas x{world}",
                    "tuning": None if tuning is None else {"line_warps": tuning[0], "cost_px": tuning[1]}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "latency_single_frame": latency,
         "clocks": clk,
         "kernel_ms_avg": {k: round(v, 4) for k, v in sorted(avg.items())},
         "paper_context": {"sdsgm_ms_per_frame": 50, "hardware": "Jetson Orin NX 16GB", "data": "KITTI 141"},

@@ -162,6 +162,14 @@ sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *r
 sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
                                     const float *sparse_lidar_disp, int16_t *out_disp);
 
+/* sgmf_compute_host_batch without the wait: copies in, pipeline and copy out
+ * are enqueued on the context's stream and the call returns; the host
+ * buffers must stay untouched (and `out` unread) until sgmf_sync(c).  With
+ * PINNED host buffers the copies run asynchronously, so two contexts on two
+ * streams overlap one batch's copies with the other's kernels. */
+sgmf_status sgmf_compute_host_batch_async(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
+                                          const float *lidar, int16_t *out);
+
 /* Wait for the context's stream and report the first asynchronous error:
  * SGMF_ERR_TIMEOUT if a bounded device wait gave up, SGMF_ERR_CUDA for a
  * CUDA error.  The timeout flag is cleared by this call. */

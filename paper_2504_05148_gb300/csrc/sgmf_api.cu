@@ -409,8 +409,9 @@ extern "C" sgmf_status sgmf_sync(sgmf_ctx *c) {
   return SGMF_OK;
 }
 
-extern "C" sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int nf, const uint8_t *left, const uint8_t *right,
-                                               const float *lidar, int16_t *out) {
+// the host entry point's work, enqueued on the context's stream (no wait)
+static sgmf_status enqueue_host_batch(sgmf_ctx *c, int nf, const uint8_t *left, const uint8_t *right,
+                                      const float *lidar, int16_t *out) {
   if (!c) return SGMF_ERR_ARG;
   if (!left || !right || !out) return fail(c, SGMF_ERR_ARG, "sgmf_compute_host: NULL image or output pointer");
   if (nf < 1 || nf > c->nb)
@@ -430,7 +431,18 @@ extern "C" sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int nf, const uint8_
   sgmf_status st = sgmf_compute_batch(c, nf, c->st_left, c->st_right, lidar ? c->st_lidar : nullptr, c->st_out);
   if (st != SGMF_OK) return st;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->st_out, n * 2, cudaMemcpyDeviceToHost, s));
-  return sgmf_sync(c);
+  return SGMF_OK;
+}
+
+extern "C" sgmf_status sgmf_compute_host_batch(sgmf_ctx *c, int nf, const uint8_t *left, const uint8_t *right,
+                                               const float *lidar, int16_t *out) {
+  const sgmf_status st = enqueue_host_batch(c, nf, left, right, lidar, out);
+  return st != SGMF_OK ? st : sgmf_sync(c);
+}
+
+extern "C" sgmf_status sgmf_compute_host_batch_async(sgmf_ctx *c, int nf, const uint8_t *left, const uint8_t *right,
+                                                     const float *lidar, int16_t *out) {
+  return enqueue_host_batch(c, nf, left, right, lidar, out);
 }
 
 extern "C" sgmf_status sgmf_compute_host(sgmf_ctx *c, const uint8_t *left, const uint8_t *right,

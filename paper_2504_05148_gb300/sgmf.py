@@ -37,7 +37,7 @@ EXPORTS = (
     "sgmf_multi_device_bytes", "sgmf_multi_destroy",
     "sgmf_server_create", "sgmf_server_add_camera", "sgmf_server_submit", "sgmf_server_poll",
     "sgmf_server_stats", "sgmf_server_destroy",
-    "sgmf_create_banded", "sgmf_compute_banded", "sgmf_band_width",
+    "sgmf_create_banded", "sgmf_compute_banded", "sgmf_band_width", "sgmf_compute_host_batch_async",
     "sgmf_compute_front", "sgmf_prior_device", "sgmf_compute_banded_back",
     "sgmf_bn_pack", "sgmf_bn_conv", "sgmf_bn_wgrad", "sgmf_bn_input", "sgmf_bn_labels", "sgmf_bn_loss",
     "sgmf_bn_adam", "sgmf_bn_tiles",
@@ -124,6 +124,7 @@ def lib(path: str | None = None):
         "sgmf_batch_capacity": (i, [P]),
         "sgmf_compute_batch": (i, [P, i, P, P, P, P]),
         "sgmf_compute_host_batch": (i, [P, i, P, P, P, P]),
+        "sgmf_compute_host_batch_async": (i, [P, i, P, P, P, P]),
         "sgmf_set_params": (i, [P, prm_p]),
         "sgmf_get_params": (i, [P, prm_p]),
         "sgmf_set_stream": (i, [P, P]),
@@ -250,6 +251,11 @@ def sgmf_compute_batch(ctx: int, n: int, left: int, right: int, lidar: int | Non
 def sgmf_compute_host_batch(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int) -> None:
     """n frames, contiguous [n][H][W] host buffers.  Waits for the result."""
     _check(lib().sgmf_compute_host_batch(ctx, n, left, right, lidar or None, out), ctx)
+
+
+def sgmf_compute_host_batch_async(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int) -> None:
+    """As sgmf_compute_host_batch, without waiting (sgmf_sync waits); pinned host buffers."""
+    _check(lib().sgmf_compute_host_batch_async(ctx, n, left, right, lidar or None, out), ctx)
 
 
 def sgmf_compute_host(ctx: int, left: int, right: int, lidar: int | None, out: int) -> None:
