@@ -375,10 +375,21 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   // are consecutive words, free of bank conflicts
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int npx = min(PX, W - x0);
+  // warp-uniform fast path: every d of the pixel has x - d >= 0, all cells are
+  // real disparities, and without a prior C-bar = H (no table)
+  const bool inner = x0 >= Dp - 1 && k.D == Dp;
   for (int px = warp; px < npx; px += 8) {
     const int x = x0 + px;
     const CT c = cl_s[px];
     const int pd = pd_s[px];
+    if (inner && pd < 0) {
+#pragma unroll
+      for (int j = 0; j < DPL; ++j) {
+        const int d = lane + 32 * j;
+        out_s[px * Dp + d] = (uint8_t)hamming<CT>(c, cr_s[px - d + Dp - 1]);
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
       const int d = lane + 32 * j;
