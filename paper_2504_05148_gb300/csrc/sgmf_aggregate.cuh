@@ -234,6 +234,7 @@ struct BandState {
   int x = 0, y = 0;              // pixel of the next step
   int dx = 0, dy = 0;            // per-step move
   int tile = -1, cur = 0;        // tile and band start of the last step
+  int kb_lo = -1;                // band start the row kernel's key bytes were built for
   uint16_t *buf = nullptr;       // the group's shared scratch, 16 * CPL cells
 };
 
@@ -258,9 +259,10 @@ __device__ __forceinline__ void band_shift(uint32_t (&L)[CPL / 2], int delta, ui
 }
 
 // the band bookkeeping of one step at (bs.x, bs.y), then the move to the next
-// pixel of the line (x wraps for the diagonals).  Called by all 32 lanes.
+// pixel of the line (x wraps for the diagonals).  Called by all 32 lanes;
+// returns the change of the band start (0 for an inactive lane).
 template <int CPL>
-__device__ __forceinline__ void band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig) {
+__device__ __forceinline__ int band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig) {
   int delta = 0;
   if (active) {
     const int t = (bs.y >> kBandTileLog) * bs.tw + (bs.x >> kBandTileLog);
@@ -275,6 +277,37 @@ __device__ __forceinline__ void band_step(BandState &bs, uint32_t (&L)[CPL / 2],
   bs.y += bs.dy;
   bs.x += bs.dx;
   bs.x = bs.x >= W ? bs.x - W : (bs.x < 0 ? bs.x + W : bs.x);
+  return delta;
+}
+
+// Banded right view.  At pixel x with band start lo, accumulator slot s holds
+// the best key of right pixel x - lo - s.  From the previous pixel (x -/+ 1,
+// band start lo - delta) slot s takes old slot s + sigma with sigma = delta - 1
+// walking right and delta + 1 walking left; old slots that fall outside the
+// band window are min-merged into merge[x'] (their right pixel may still get
+// cells from pixels farther along, which merge there too).  Runs on all 32
+// lanes through the group's shared buffer abuf (16 * CPL words).
+template <int CPL>
+__device__ __forceinline__ void band_acc_shift(uint32_t (&acc)[CPL], int sigma, int xr0, int W, uint32_t *abuf,
+                                               uint32_t *merge, int lig) {
+  constexpr int B = 16 * CPL;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int sl = lig * CPL + j;
+    abuf[sl] = acc[j];
+    const int to = sl - sigma;                     // the new slot of old slot sl
+    if ((unsigned)to >= (unsigned)B && acc[j] != 0xffffffffu) {
+      const int xr = xr0 - sl;                     // its right pixel
+      if ((unsigned)xr < (unsigned)W) atomicMin(&merge[xr], acc[j]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int src = lig * CPL + j + sigma;
+    acc[j] = (unsigned)src < (unsigned)B ? abuf[src] : 0xffffffffu;
+  }
+  __syncwarp();
 }
 
 // Bounded wait for ring fill g (stage g % S, phase g / S).  The decision is
@@ -544,7 +577,6 @@ struct RowArgs {
   StepConsts sc;
   const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]
   int tw, th;
-  uint16_t *sum;          // banded mode: S of every frame, [frame][H][W][Dp]
 };
 
 template <int CPL, bool S8>
@@ -579,10 +611,10 @@ struct RowGeom {
 // RESTART: the chunk holds the first step of a walk
 template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART, bool BANDED>
 __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, const uint8_t *stg, int xl, int t_lo,
-                                          int t_hi, const uint32_t (&z)[CPL / 4], const uint32_t (&kb)[CPL / 2],
+                                          int t_hi, const uint32_t (&z)[CPL / 4], uint32_t (&kb)[CPL / 2],
                                           const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp, int lig,
                                           uint8_t *spill_lane, int16_t *dstar, int16_t *dprime, int16_t *dsub,
-                                          uint16_t *dbg_lane, uint32_t *merge, BandState &bs) {
+                                          uint16_t *dbg_lane, uint32_t *merge, BandState &bs, uint32_t *abuf) {
   using CF = RowCfg<CPL, S8>;
   constexpr int NW = CPL / 2, Dp = CF::Dp, SB = CF::SB;
   const uint8_t *cst = stg + lig * CPL;
@@ -594,9 +626,17 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
     const int r = valid ? x - xl : 0;
     uint32_t C[NW];
     unpack_u8<CPL>(cst + r * Dp, z, C);
+    int delta = 0;
     if (BANDED) {
       bs.x = x;   // rows: the tile follows x (bs.y is the row)
-      band_step<CPL>(bs, w.L, valid, g.W, lig);
+      delta = band_step<CPL>(bs, w.L, valid, g.W, lig);
+      if (SECOND && bs.cur != bs.kb_lo) {
+        // keys carry absolute disparities: lo + slot
+        bs.kb_lo = bs.cur;
+        const uint32_t b0 = (uint32_t)(bs.cur + lig * CPL);
+#pragma unroll
+        for (int i = 0; i < CPL / 2; ++i) kb[i] = (b0 + 2 * i) | ((b0 + 2 * i + 1) << 8);
+      }
     }
     if (RESTART) {
       // a walk starts at x = 0 (group 0) / x = W-1 (group 1): zero previous vector
@@ -623,7 +663,6 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
       for (int i = 0; i < NW; ++i) Sm[i] += T[i];
     }
     if (dbg_lane != nullptr && valid) store_u16<CPL>(dbg_lane + (size_t)x * Dp, Sm);
-    if (BANDED) continue;   // banded mode: S goes out (dbg_lane), WTA runs in its own kernel
     // keys (S << 8 | d); padding keys have 0xff in the top byte
     uint32_t key[CPL];
 #pragma unroll
@@ -660,6 +699,42 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
         }
         dsub[g.row + x] = (int16_t)v;
       }
+    }
+    if (BANDED) {
+      // right view on the bands: re-index the accumulator to this pixel's
+      // window (emitting the slots that leave it), then fold in S(x, d)
+      const int xr0 = (g.fwd ? x - 1 : x + 1) - (bs.cur - delta);   // right pixel of old slot 0
+      if (__any_sync(kFull, delta != 0)) {
+        const int sigma = g.fwd ? delta - 1 : delta + 1;
+        band_acc_shift<CPL>(w.acc, valid ? sigma : 0, valid ? xr0 : -0x40000000, g.W, abuf, merge, lig);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) w.acc[j] = min(w.acc[j], key[j]);
+        }
+      } else {
+        // same band as the previous pixel: the plain one-slot move, and the
+        // slot that leaves the window goes to the merge array
+        const uint32_t sh_up = __shfl_up_sync(kFull, w.acc[CPL - 1], 1, 16);
+        const uint32_t sh_dn = __shfl_down_sync(kFull, w.acc[0], 1, 16);
+        if (valid) {
+          const int eslot = g.fwd ? 16 * CPL - 1 : 0;
+          const uint32_t out = g.fwd ? w.acc[CPL - 1] : w.acc[0];
+          if (lig == (g.fwd ? 15 : 0) && out != 0xffffffffu && (unsigned)(xr0 - eslot) < (unsigned)g.W)
+            atomicMin(&merge[xr0 - eslot], out);
+          const uint32_t in_up = lig == 0 ? 0xffffffffu : sh_up;
+          const uint32_t in_dn = lig == 15 ? 0xffffffffu : sh_dn;
+          uint32_t nacc[CPL];
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const uint32_t lower = j == 0 ? in_up : w.acc[j - 1];
+            const uint32_t upper = j == CPL - 1 ? in_dn : w.acc[j + 1];
+            nacc[j] = min(g.fwd ? lower : upper, key[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) w.acc[j] = nacc[j];
+        }
+      }
+      continue;
     }
     // right view: group 0 (x rising) moves keys up a slot per step, group 1
     // (x falling) down a slot; both fold in S(x, d)
@@ -728,13 +803,16 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
   int16_t *dsub = a.dsub != nullptr ? a.dsub + f * fpx : nullptr;
   uint16_t *dbg_lane = (f == 0 && a.dbg_sum != nullptr) ? a.dbg_sum + g.row * Dp + lig * CPL : nullptr;
   BandState bs;
+  uint32_t *abuf = nullptr;
   if (BANDED) {
-    // S of every frame goes out; the shift scratch takes the merge area (unused here)
-    dbg_lane = a.sum + f * fcells + g.row * Dp + lig * CPL;
+    // shared memory after the merge array (one word per right pixel of the
+    // row): each group's path-cost shift buffer, then its accumulator buffer
     bs.lo = a.lo + (size_t)f * a.th * a.tw;
     bs.tw = a.tw;
     bs.y = y;
-    bs.buf = reinterpret_cast<uint16_t *>(merge) + grp * Dp;
+    uint16_t *lbuf = reinterpret_cast<uint16_t *>(merge + W);
+    bs.buf = lbuf + grp * Dp;
+    abuf = reinterpret_cast<uint32_t *>(lbuf + 2 * Dp) + grp * Dp;
   }
   // the row spill region of this frame
   uint8_t *spill = static_cast<uint8_t *>(a.spill) + f * 4 * fcells * 2 + 3 * fcells * SB;
@@ -742,7 +820,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
   const int tmid = g.xm + g.delay;         // both first halves end here
   const int T = W + g.delay;               // lockstep steps
   const int c1 = (tmid + K - 1) / K, c2 = (T - tmid + K - 1) / K, nch = c1 + c2;
-  for (int i = lane; i < kMaxDisp; i += 32) merge[i] = 0xffffffffu;
+  for (int i = lane; i < (BANDED ? W : kMaxDisp); i += 32) merge[i] = 0xffffffffu;
   if (lane == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
@@ -827,7 +905,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
     const bool restart = t_lo <= g.delay && 0 < t_hi;
 #define ROW_CHUNK(SEC, RS)                                                                                   \
   row_chunk<CPL, S8, NP, FULLD, SEC, RS, BANDED>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp,  \
-                                                 lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs)
+                                                 lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs, abuf)
     if (c < c1) {
       if (restart) ROW_CHUNK(false, true); else ROW_CHUNK(false, false);
     } else {
@@ -841,7 +919,22 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
       __syncwarp();
     }
   }
-  if (BANDED) return;
+  if (BANDED) {
+    if (ok) {
+      // the slots still held at the end of each walk, then d' of every right
+      // pixel from the merged keys (-1 where no band holds a cell of its diagonal)
+      const int xr0 = (g.fwd ? W - 1 : 0) - bs.cur;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int xr = xr0 - (lig * CPL + j);
+        if (w.acc[j] != 0xffffffffu && (unsigned)xr < (unsigned)W) atomicMin(&merge[xr], w.acc[j]);
+      }
+      __syncwarp();
+      for (int i = lane; i < W; i += 32)
+        dprime[g.row + i] = merge[i] == 0xffffffffu ? (int16_t)-1 : (int16_t)(merge[i] & 0xffu);
+    }
+    return;
+  }
   if (ok && g.fwd) {
     // right pixels x' = W-1-d whose diagonal leaves the image: slot d of group 0
 #pragma unroll
@@ -936,10 +1029,14 @@ cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStrea
 template <int CPL, bool S8, int NP, bool FULLD, bool BANDED>
 static cudaError_t launch_rows_v(const RowArgs &a, int nf, cudaStream_t s) {
   using CF = RowCfg<CPL, S8>;
+  // banded: the merge array grows to one word per pixel of the row, followed
+  // by the two groups' shift buffers (u16 path costs, u32 accumulators)
+  constexpr int kBandMax = CF::kSmem - kMaxDisp * 4 + kMaxDim * 4 + 2 * CF::Dp * 2 + 2 * CF::Dp * 4;
+  const int smem = BANDED ? CF::kSmem - kMaxDisp * 4 + a.k.W * 4 + 2 * CF::Dp * 2 + 2 * CF::Dp * 4 : CF::kSmem;
   static bool done[64] = {};
-  cudaError_t e = smem_optin(k_agg_rows<CPL, S8, NP, FULLD, BANDED>, CF::kSmem, done);
+  cudaError_t e = smem_optin(k_agg_rows<CPL, S8, NP, FULLD, BANDED>, BANDED ? kBandMax : CF::kSmem, done);
   if (e != cudaSuccess) return e;
-  k_agg_rows<CPL, S8, NP, FULLD, BANDED><<<dim3(a.k.H, nf), 32, CF::kSmem, s>>>(a);
+  k_agg_rows<CPL, S8, NP, FULLD, BANDED><<<dim3(a.k.H, nf), 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -960,7 +1057,6 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
   a.lo = b.band_lo;
   a.tw = k.tw;
   a.th = k.th;
-  a.sum = b.band_sum;
   if (k.band) {
     if constexpr (CPL <= 8) {
       if (k.num_paths == 8) return launch_rows_v<CPL, S8, 3, true, true>(a, nf, s);

@@ -168,7 +168,7 @@ static void apply_params(sgmf_ctx *c, const sgmf_params &p) {
 static void free_all(sgmf_ctx *c) {
   void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.dsub, c->b.censL,
                   c->b.censR, c->b.pres, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
-                  c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.band_lo, c->b.band_sum, c->b.err, c->st_left,
+                  c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.band_lo, c->b.err, c->st_left,
                   c->st_right, c->st_lidar, c->st_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -244,7 +244,6 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), 4 * nv * 2));
   if (band) {
     A(dalloc(c, &c->b.band_lo, (size_t)k.tw * k.th * max_batch * 2));
-    A(dalloc(c, &c->b.band_sum, nv * 2));
   }
   A(dalloc(c, &c->b.err, sizeof(int)));
   if (e == cudaSuccess) e = cudaMemset(c->b.err, 0, sizeof(int));
@@ -327,7 +326,7 @@ extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (c->k.semidense) n += 3;
   if (need_boxc(c->k)) n += 2;
   n += 1;      // consistency
-  if (c->k.band) n += 2;   // band clamp, banded WTA
+  if (c->k.band) n += 1;   // band clamp
   return n;
 }
 
@@ -483,7 +482,7 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
   if (bytes < need) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: need %zu bytes, got %zu", need, bytes);
   if (stage == SGMF_STAGE_DSUB && !k.subpixel)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: DSUB needs subpixel = 1");
-  if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum && !k.band)
+  if (stage == SGMF_STAGE_SUM && !c->b.dbg_sum)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: SUM needs sgmf_set_debug(c, 1) before sgmf_compute");
   sgmf_status st = sgmf_sync(c);
   if (st != SGMF_OK) return st;
@@ -513,7 +512,7 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
       break;
     case SGMF_STAGE_SUM:
       if (k.band) {   // banded: [H][W][band], cell j = disparity lo_p + j
-        CUDA_TRY(c, cudaMemcpy(dst, c->b.band_sum, need, cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(dst, c->b.dbg_sum, need, cudaMemcpyDeviceToHost));
         break;
       }
       CUDA_TRY(c, cudaMemcpy2D(dst, (size_t)k.D * 2, c->b.dbg_sum, (size_t)k.Dp * 2, (size_t)k.D * 2, n,
@@ -674,10 +673,8 @@ extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_
   LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
   mark(c, "agg_lines");
   LAUNCH_TRY(c, launch_agg_lines(k, c->b, n, c->spill8, s));
-  mark(c, "agg_rows");
+  mark(c, "agg_rows_wta");
   LAUNCH_TRY(c, launch_agg_rows(k, c->b, n, c->spill8, s));
-  mark(c, "wta");
-  LAUNCH_TRY(c, launch_wta_banded(k, c->b, n, s));
   if (need_boxc(k)) {
     mark(c, "boxor_check");
     LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s));

@@ -1,8 +1,8 @@
 // sgmf_band.cu -- kernels of the banded mode (not in the paper): the method
 // restricted to a disparity band [lo_p, lo_p + B) per pixel, lo_p constant on
-// kBandTile x kBandTile pixel tiles.  Ingest, census, semidensification and the check are
-// the plain kernels; the cost, the aggregation (sgmf_aggregate.cuh, BANDED
-// variants) and the WTA work on the bands.
+// kBandTile x kBandTile pixel tiles.  Ingest, census, semidensification and
+// the check are the plain kernels; the cost (here) and the aggregation with
+// its WTA (sgmf_aggregate.cuh, BANDED variants) work on the bands.
 #include <cstdint>
 
 #include "sgmf_internal.cuh"
@@ -68,11 +68,25 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // every pixel of the CTA has x - d >= 0 for all its band cells
+  const bool inner = x0 >= lo_max + B - 1;
   for (int px = warp; px < npx; px += 8) {
     const int x = x0 + px;
     const CT c = cl_s[px];
     const int pd = pd_s[px];
     const int lo = lo_s[px >> kBandTileLog];
+    if (inner && pd < 0) {   // warp-uniform: without a prior C-bar = H
+#pragma unroll
+      for (int m = 0; m < B / 32; ++m) {
+        const int j = lane + 32 * m;
+        const CT r = cr_s[x - (lo + j) - base];
+        if constexpr (sizeof(CT) == 4)
+          out_s[px * B + j] = (uint8_t)__popc(c ^ r);
+        else
+          out_s[px * B + j] = (uint8_t)__popcll(c ^ r);
+      }
+      continue;
+    }
 #pragma unroll
     for (int m = 0; m < B / 32; ++m) {
       const int j = lane + 32 * m, d = lo + j;
@@ -111,62 +125,6 @@ cudaError_t launch_cost_banded(const KParams &k, const Buffers &b, int nf, cudaS
     launch_cost_banded_t<uint64_t>(k, b, nf, tab, s);
   else
     launch_cost_banded_t<uint32_t>(k, b, nf, tab, s);
-  return cudaGetLastError();
-}
-
-// Banded WTA from S: d*_p = lo_p + argmin_j S(p, j) (ties: smaller d), and
-// d'(x') = argmin over the cells (x' + d, d) inside the bands (ties: smaller
-// d), or -1 where no band holds such a cell.  One CTA per row: a warp takes
-// one pixel at a time (lanes over its B cells), keys S << 8 | d; the
-// right-view keys are min-merged in shared memory with atomicMin.
-template <int B>
-__global__ void __launch_bounds__(256) k_wta_banded(KParams k, Buffers b0) {
-  extern __shared__ uint32_t keys[];   // [W]
-  const Buffers b = frame_view(k, b0, blockIdx.y);
-  const int y = blockIdx.x, W = k.W;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) keys[i] = 0xffffffffu;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int CL = B / 32;   // cells per lane: 2 or 4
-  const int16_t *lo_row = b.band_lo + (size_t)(y >> kBandTileLog) * k.tw;
-  for (int x = warp; x < W; x += 8) {
-    const int lo = lo_row[x >> kBandTileLog];
-    const uint16_t *sp = b.band_sum + ((size_t)y * W + x) * B + lane * CL;
-    uint32_t v[CL];
-    if constexpr (CL == 2) {
-      const uint32_t t = *reinterpret_cast<const uint32_t *>(sp);
-      v[0] = t & 0xffffu;
-      v[1] = t >> 16;
-    } else {
-      const uint2 t = *reinterpret_cast<const uint2 *>(sp);
-      v[0] = t.x & 0xffffu;
-      v[1] = t.x >> 16;
-      v[2] = t.y & 0xffffu;
-      v[3] = t.y >> 16;
-    }
-    uint32_t best = 0xffffffffu;
-#pragma unroll
-    for (int i = 0; i < CL; ++i) {
-      const int d = lo + lane * CL + i;
-      const uint32_t key = (v[i] << 8) | (uint32_t)d;
-      best = min(best, key);
-      if (x - d >= 0) atomicMin(&keys[x - d], key);
-    }
-    best = __reduce_min_sync(0xffffffffu, best);
-    if (lane == 0) b.dstar[(size_t)y * W + x] = (int16_t)(best & 0xffu);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < W; i += blockDim.x)
-    b.dprime[(size_t)y * W + i] = keys[i] == 0xffffffffu ? (int16_t)-1 : (int16_t)(keys[i] & 0xffu);
-}
-
-cudaError_t launch_wta_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
-  dim3 grid(k.H, nf);
-  const size_t sm = (size_t)k.W * 4;
-  if (k.band == 64)
-    k_wta_banded<64><<<grid, 256, sm, s>>>(k, b);
-  else
-    k_wta_banded<128><<<grid, 256, sm, s>>>(k, b);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,6 @@ struct Buffers {   // base pointers of frame 0
   uint16_t *dbg_sum;          // [H][W][Dp] or null
   int *err;                   // device error word
   int16_t *band_lo;           // banded mode: band start per tile, [frame][th][tw] (clamped copy)
-  uint16_t *band_sum;         // banded mode: S, [frame][H][W][Dp]
 };
 
 // per-frame element counts
@@ -86,7 +85,6 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
   v.spill = static_cast<uint8_t *>(b.spill) + f * 4 * cells * 2;
   v.dbg_sum = (b.dbg_sum != nullptr && f == 0) ? b.dbg_sum : nullptr;
   v.band_lo = b.band_lo ? b.band_lo + (size_t)f * k.th * k.tw : nullptr;
-  v.band_sum = b.band_sum ? b.band_sum + f * cells : nullptr;
   return v;
 }
 
@@ -189,7 +187,6 @@ cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool sp
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const int16_t *lo_in, cudaStream_t s);
 cudaError_t launch_cost_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
-cudaError_t launch_wta_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);
 
 // host: parameter rules of sgmf_set_params (SGMF_OK or SGMF_ERR_PARAM with a reason)

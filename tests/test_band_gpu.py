@@ -21,6 +21,7 @@ def _gpu(scene, B, lo_tiles, params=None, lidar=True):
     dev = torch.device("cuda:0")
     ctx = S.Context(scene.W, scene.H, scene.D, params, band=B)
     try:
+        ctx.set_debug(True)          # keeps the banded S of the frame for the comparison
         out = torch.empty(scene.shape, dtype=torch.int16, device=dev)
         ctx.compute_banded(torch.from_numpy(scene.left).to(dev), torch.from_numpy(scene.right).to(dev),
                            torch.from_numpy(scene.lidar).to(dev) if lidar else None,
