@@ -319,7 +319,7 @@ int sgmf_band_width(const sgmf_ctx *c);
  * Launch shapes only: every choice gives bit-identical results. */
 typedef struct {
     int32_t line_warps;   /* warps per CTA of the vertical/diagonal line kernels
-                             (each warp walks two lines): 2, 4 (default) or 8 */
+                             (each warp walks two lines): 1, 2, 4 (default) or 8 */
     int32_t cost_px;      /* pixels of one row per CTA of the cost kernel: 32, 64 or
                              128 (default) */
 } sgmf_tuning;
@@ -329,7 +329,7 @@ sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t);
 sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t);
 
 /* Autotuner.  Runs sgmf_compute_batch(c, n, left, right, lidar, out) on the
- * caller's DEVICE frames once per candidate (all 3 x 3 tunings) as a
+ * caller's DEVICE frames once per candidate (all 4 x 3 tunings) as a
  * warm-up, then `reps` timed runs (CUDA events on the context's stream,
  * 1 <= reps <= 100); keeps the candidate with the smallest median time in
  * the context and returns it in *best and its median in *best_ms (either may

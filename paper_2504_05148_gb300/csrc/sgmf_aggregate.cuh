@@ -982,7 +982,7 @@ static cudaError_t launch_line_family_w(const LineArgs &a, int nf, cudaStream_t 
   return cudaGetLastError();
 }
 
-// warps per CTA from the context's tuning (2, 4 or 8); the banded variant
+// warps per CTA from the context's tuning (1, 2, 4 or 8); the banded variant
 // exists for 4 warps and up to 8 cells per lane (bands of 64 or 128)
 template <int CPL, bool S8, int FAM>
 static cudaError_t launch_line_family(const LineArgs &a, int nf, cudaStream_t s) {
@@ -991,6 +991,7 @@ static cudaError_t launch_line_family(const LineArgs &a, int nf, cudaStream_t s)
     return cudaErrorInvalidValue;
   }
   switch (a.k.line_warps) {
+    case 1: return launch_line_family_w<CPL, S8, FAM, 1, false>(a, nf, s);
     case 2: return launch_line_family_w<CPL, S8, FAM, 2, false>(a, nf, s);
     case 8: return launch_line_family_w<CPL, S8, FAM, 8, false>(a, nf, s);
     default: return launch_line_family_w<CPL, S8, FAM, 4, false>(a, nf, s);

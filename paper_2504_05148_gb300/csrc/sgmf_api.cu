@@ -549,14 +549,14 @@ extern "C" size_t sgmf_device_bytes(const sgmf_ctx *c) { return c ? c->bytes : 0
 
 // ---- launch tuning -------------------------------------------------------------
 static bool valid_tuning(const sgmf_tuning &t) {
-  return (t.line_warps == 2 || t.line_warps == 4 || t.line_warps == 8) &&
+  return (t.line_warps == 1 || t.line_warps == 2 || t.line_warps == 4 || t.line_warps == 8) &&
          (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128);
 }
 
 extern "C" sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t) {
   if (!c || !t) return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: NULL argument");
   if (!valid_tuning(*t))
-    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: need line_warps in {2,4,8} and cost_px in {32,64,128}");
+    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: need line_warps in {1,2,4,8} and cost_px in {32,64,128}");
   c->k.line_warps = t->line_warps;
   c->k.cost_px = t->cost_px;
   return SGMF_OK;
@@ -584,9 +584,9 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     st = fail(c, SGMF_ERR_CUDA, "sgmf_autotune: cudaEventCreate failed");
   }
-  const int warps[3] = {2, 4, 8}, pxs[3] = {32, 64, 128};
+  const int warps[4] = {1, 2, 4, 8}, pxs[3] = {32, 64, 128};
   std::vector<float> t;
-  for (int i = 0; i < 9 && st == SGMF_OK; ++i) {
+  for (int i = 0; i < 12 && st == SGMF_OK; ++i) {
     c->k.line_warps = warps[i / 3];
     c->k.cost_px = pxs[i % 3];
     st = sgmf_compute_batch(c, n, left, right, lidar, out);   // warm-up (and first-use attributes)

@@ -15,7 +15,7 @@ from paper_2504_05148_gb300 import sgmf as S
 
 pytestmark = pytest.mark.gpu
 
-TUNINGS = [(w, px) for w in (2, 4, 8) for px in (32, 64, 128)]
+TUNINGS = [(w, px) for w in (1, 2, 4, 8) for px in (32, 64, 128)]
 
 
 def _run(scene, params, tuning):
@@ -56,7 +56,7 @@ def test_tunings_agree_at_full_size(gpu):
 def test_bad_tuning_rejected(gpu):
     ctx = S.Context(64, 32, 32)
     try:
-        for t in [(3, 128), (4, 100), (0, 0), (16, 64)]:
+        for t in [(3, 128), (4, 100), (0, 0), (16, 64), (1, 16)]:
             with pytest.raises(S.SgmfError) as e:
                 S.sgmf_set_tuning(ctx.handle, *t)
             assert e.value.status == S.SGMF_ERR_ARG
