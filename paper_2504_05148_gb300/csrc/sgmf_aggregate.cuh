@@ -343,7 +343,8 @@ struct LineCfg {
   static constexpr int SB = S8 ? 1 : 2;        // spill bytes per cell
   static constexpr int kCost = K * 2 * Dp;     // [row][line of the warp][Dp]
   static constexpr int kSpillLine = K * Dp * SB;
-  static constexpr int kStage = kCost + 2 * kSpillLine;
+  // S8: the up pass reads no spill (each pass writes its own byte plane)
+  static constexpr int kStage = kCost + (S8 ? 0 : 2 * kSpillLine);
   static constexpr int kWarp = S * kStage;
   static constexpr int kWarps = NWARP;         // warps (two lines each) per CTA: a tuning choice
   static constexpr int kSmem = kWarps * kWarp + kWarps * S * 8;
@@ -363,14 +364,20 @@ __device__ __forceinline__ int line_x(int fam, int k, int y, int W) {
 template <int CPL, bool S8, int FAM, bool DOWN, bool FAST, bool BANDED>
 __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *sstl, int n, uint32_t (&L)[CPL / 2],
                                            uint32_t &mm, int &togo, int &next_len, int seg_full,
-                                           uint8_t *&sp, uint16_t *&pp, const uint32_t (&z)[CPL / 4],
+                                           uint8_t *&sp, uint8_t *&pp, const uint32_t (&z)[CPL / 4],
                                            const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp,
-                                           bool active, int y_hi, int y_first, int W, uint16_t *part_lane,
+                                           bool active, int y_hi, int y_first, int W, uint8_t *part_lane,
                                            BandState &bs, int lig) {
   constexpr int NW = CPL / 2, Dp = 16 * CPL, SB = S8 ? 1 : 2;
-  // partial-sum pointer step moving up one row (x - 1, x, x + 1 for families 1, 0, 2)
+  // The family buffer holds 2 Dp bytes per pixel: with S8 the down pass's
+  // byte vector then the up pass's (pp walks this pass's half), otherwise the
+  // u16 pair sum that the up pass forms from the down pass's spill (sp).
+  constexpr int PS = 2 * Dp;
+  // pixel pointer step per row: x - 1, x, x + 1 (families 1, 0, 2) going up,
+  // the reverse going down
   constexpr int kDelta = FAM == 0 ? 0 : (FAM == 1 ? -1 : 1);
-  const ptrdiff_t up_step = (ptrdiff_t)(kDelta - W) * Dp;
+  const ptrdiff_t up_step = (ptrdiff_t)(kDelta - W) * PS;
+  const ptrdiff_t down_step = (ptrdiff_t)(W - kDelta) * PS;
   uint32_t C[NW];
 #pragma unroll 2
   for (int i = 0; i < n; ++i) {
@@ -386,18 +393,27 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
       if (start) {
         togo = next_len;
         next_len = seg_full;
-        // going up, a diagonal line restarts (after its first pixel) where x
-        // wrapped around: x = W-1 for family 1, x = 0 for family 2
+        // a diagonal line restarts (after its first pixel) where x wrapped
+        // around: going up at x = W-1 for family 1, x = 0 for family 2;
+        // going down at x = 0 for family 1, x = W-1 for family 2
         if (!DOWN && FAM != 0) {
           const int y = y_hi - i;
-          if (y != y_first) pp = part_lane + (size_t)(y * W + (FAM == 1 ? W - 1 : 0)) * Dp;
+          if (y != y_first) pp = part_lane + (size_t)(y * W + (FAM == 1 ? W - 1 : 0)) * PS;
+        }
+        if (S8 && DOWN && FAM != 0) {
+          const int y = y_hi - (n - 1) + i;
+          if (y != 0) pp = part_lane + (size_t)(y * W + (FAM == 1 ? 0 : W - 1)) * PS;
         }
       }
       --togo;
     }
     sgm_step<NW>(L, C, mm, sc, edge_lo, edge_hi);
     mm = group_min<NW>(L, grp);
-    if (DOWN) {
+    if constexpr (S8) {
+      // this direction's path costs, one byte per cell, in its half of the pixel's slot
+      if (active) store_u8<CPL>(pp, L);
+      pp += DOWN ? down_step : up_step;
+    } else if (DOWN) {
       if (active) spill_put<CPL, S8>(sp, L);
       sp += Dp * SB;
     } else {
@@ -405,7 +421,7 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
       spill_get<CPL, S8>(sstl + r * Dp * SB, Ld);
 #pragma unroll
       for (int w = 0; w < NW; ++w) Ld[w] += L[w];
-      if (active) store_u16<CPL>(pp, Ld);
+      if (active) store_u16<CPL>(reinterpret_cast<uint16_t *>(pp), Ld);
       pp += up_step;
     }
   }
@@ -423,7 +439,9 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   const int W = a.k.W, H = a.k.H;
   const size_t fcells = frame_cells(a.k);
   const uint8_t *cost = a.cost + f * fcells;
-  uint16_t *part = a.part[FAM] + f * fcells;
+  // the family's buffer of this frame, 2 Dp bytes per pixel: [L_down][L_up]
+  // bytes for S8, else the u16 pair sums
+  uint8_t *part = reinterpret_cast<uint8_t *>(a.part[FAM] + f * fcells);
   const int line0 = (blockIdx.x * CF::kWarps + warp) * 2;
   if (line0 >= W) return;                    // warps are independent: no block barrier below
   const int line = line0 + grp;
@@ -458,7 +476,7 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
       y_lo = max(0, y_hi - K + 1);
       n = y_hi - y_lo + 1;
     }
-    if (lane == 0) mbar_expect_tx(&bars[stage], (uint32_t)(nact * n * Dp * (up ? 1 + SB : 1)));
+    if (lane == 0) mbar_expect_tx(&bars[stage], (uint32_t)(nact * n * Dp * (up && !S8 ? 1 + SB : 1)));
     __syncwarp();
     const int r = lane >> 1, gg = lane & 1;
     if (r < n && line0 + gg < W) {
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
       bulk_g2s(st + (r * 2 + gg) * Dp, cost + ((size_t)y * W + line_x(FAM, line0 + gg, y, W)) * Dp, Dp,
                &bars[stage]);
     }
-    if (up && lane >= 30 && line0 + (lane - 30) < W) {
+    if (!S8 && up && lane >= 30 && line0 + (lane - 30) < W) {
       const int l = lane - 30;
       bulk_g2s(st + CF::kCost + l * CF::kSpillLine,
                spill + (spill0 + (size_t)l * H * Dp + (size_t)y_lo * Dp) * SB, (uint32_t)(n * Dp * SB),
@@ -499,7 +517,8 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   int next_len = FAM == 0 ? 0x7fffffff : (FAM == 1 ? W - x_top : x_top + 1);
   {
     uint8_t *sp = spill + (spill_line + (size_t)lig * CPL) * SB;
-    uint16_t *pp = nullptr;
+    uint8_t *down_lane = part + lig * CPL;                                  // S8: the down half
+    uint8_t *pp = S8 ? down_lane + (size_t)x_top * 2 * Dp : nullptr;
     int issued = 0;
     for (int c = 0; c < nch; ++c) {
       while (issued < nch && issued < c + S) issue(issued++);
@@ -510,11 +529,11 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
       if (fast)
         line_chunk<CPL, S8, FAM, true, true, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
                                                      seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active,
-                                                     c * K + n - 1, H - 1, W, part, bs, lig);
+                                                     c * K + n - 1, H - 1, W, down_lane, bs, lig);
       else
         line_chunk<CPL, S8, FAM, true, false, BANDED>(st + cost_off, st + spill_off, n, L, mm, togo, next_len,
                                                       seg_full, sp, pp, z, sc, edge_lo, edge_hi, grp, active,
-                                                      c * K + n - 1, H - 1, W, part, bs, lig);
+                                                      c * K + n - 1, H - 1, W, down_lane, bs, lig);
       __syncwarp();
     }
   }
@@ -533,8 +552,8 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   }
   {
     uint8_t *sp = nullptr;
-    uint16_t *part_lane = part + lig * CPL;
-    uint16_t *pp = part_lane + (size_t)((H - 1) * W + x_bot) * Dp;
+    uint8_t *part_lane = S8 ? part + Dp + lig * CPL : part + lig * CPL * 2;   // S8: the up half
+    uint8_t *pp = part_lane + (size_t)((H - 1) * W + x_bot) * 2 * Dp;
     int issued = nch;
     for (int c = 0; c < nch; ++c) {
       const int g = nch + c;
@@ -619,7 +638,9 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
   constexpr int NW = CPL / 2, Dp = CF::Dp, SB = CF::SB;
   const uint8_t *cst = stg + lig * CPL;
   const uint8_t *sst = stg + CF::kCost + lig * CPL * SB;
-  const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * 2;
+  // family sums, 2 Dp bytes per pixel: u16 pair sums, or (S8) the down and
+  // up passes' byte vectors
+  const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * (S8 ? 1 : 2);
   for (int t = t_lo; t < t_hi; ++t) {
     const int x = g.fwd ? t - g.delay : g.W - 1 - t;
     const bool valid = x >= 0 && x < g.W;
@@ -658,7 +679,16 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       uint32_t T[NW];
-      load_u16<CPL>(reinterpret_cast<const uint16_t *>(pst + j * CF::kPart + r * Dp * 2), T);
+      if constexpr (S8) {
+        const uint32_t z0[CPL / 4] = {};
+        uint32_t U[NW];
+        unpack_u8<CPL>(pst + j * CF::kPart + r * 2 * Dp, z0, T);         // L_down of the family
+        unpack_u8<CPL>(pst + j * CF::kPart + r * 2 * Dp + Dp, z0, U);    // L_up
+#pragma unroll
+        for (int i = 0; i < NW; ++i) T[i] += U[i];
+      } else {
+        load_u16<CPL>(reinterpret_cast<const uint16_t *>(pst + j * CF::kPart + r * Dp * 2), T);
+      }
 #pragma unroll
       for (int i = 0; i < NW; ++i) Sm[i] += T[i];
     }
@@ -874,7 +904,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
       if (j == 0) bulk_g2s(st, cost + cell, (uint32_t)(nn * Dp), &bars[stage]);
       if (second) {
         if (j == 1) bulk_g2s(st + CF::kCost, spill + cell * SB, (uint32_t)(nn * Dp * SB), &bars[stage]);
-        if (j >= 2 && j < 2 + NP)
+        if (j >= 2 && j < 2 + NP)   // 2 Dp bytes per pixel in either layout
           bulk_g2s(st + CF::kCost + CF::kSpill + (j - 2) * CF::kPart,
                    (j == 2 ? part0 : (j == 3 ? part1 : part2)) + cell, (uint32_t)(nn * Dp * 2), &bars[stage]);
       }
