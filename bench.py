@@ -71,10 +71,25 @@ def algorithmic(name: str, V: int, N: int, num_paths: int = 8):
     return None
 
 
-def src_hash() -> str:
+# csrc files whose contents decide each timed kernel's code and launch shape
+# (the shared header and the API file that sizes the buffers go with every one)
+KERNEL_SOURCES = {
+    "agg_lines": ("sgmf_aggregate", "sgmf_agg_cpl"),
+    "agg_rows_wta": ("sgmf_aggregate", "sgmf_agg_cpl"),
+    "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor_semidense": ("sgmf_front",),
+    "semidense": ("sgmf_front",), "cost": ("sgmf_front",), "boxor_check": ("sgmf_front",),
+    "consistency": ("sgmf_check",),
+}
+
+
+def src_hash(kernel: str = None) -> str:
+    """Hash of the csrc sources: all of them, or those of one timed kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_05148_gb300", "csrc")
+    pre = None if kernel is None else KERNEL_SOURCES[kernel] + ("sgmf_internal", "sgmf_api")
     for f in sorted(os.listdir(csrc)):
+        if pre is not None and not f.startswith(pre):
+            continue
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -712,10 +727,10 @@ def main():
         t_hbm = alg["bytes"] / (peaks["hbm_gbs"] * 1e9)
         t_alu = alg["ops"] / alu_peak
         # measured DRAM bytes per frame from the committed ncu summary, valid only
-        # while the kernel sources are the ones it was captured from
+        # while the kernel's sources are the ones it was captured from
         traffic = None
         try:
-            cur = src_hash()
+            cur = src_hash(dom)
             with open(TRAFFIC_FILE) as fh:
                 for line in fh:
                     parts = line.split()
