@@ -76,8 +76,8 @@ def algorithmic(name: str, V: int, N: int, num_paths: int = 8):
 KERNEL_SOURCES = {
     "agg_lines": ("sgmf_aggregate", "sgmf_agg_cpl"),
     "agg_rows_wta": ("sgmf_aggregate", "sgmf_agg_cpl"),
-    "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor_semidense": ("sgmf_front",),
-    "semidense": ("sgmf_front",), "cost": ("sgmf_front",), "boxor_check": ("sgmf_front",),
+    "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor": ("sgmf_front",),
+    "semidense": ("sgmf_front",), "cost": ("sgmf_front",),
     "consistency": ("sgmf_check",),
 }
 
@@ -321,7 +321,8 @@ def run_mixed(args, rank, world):
     if rank != 0:
         m.close()
         return 0
-    classes = [{"shape": list(sh), "frames": n, "line_warps": t[0], "cost_px": t[1]} for sh, n, t in m.classes()]
+    classes = [{"shape": list(sh), "frames": n, "line_warps": t[0], "cost_px": t[1], "sweep": t[2]}
+               for sh, n, t in m.classes()]
     line = {
         "metric": "W*H*D/s and frames/s, 48 mixed-size pairs per graph launch", "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -369,6 +370,9 @@ def run_serve(args, rank, world):
     sat = serving.run_closed(cams, duration_s=max(2.0, args.serve_seconds / 3), depth=4, **kw)
     clk = clocks.stop()
     ps, ss = paced.summary(), sat.summary()
+    probe = sgmf.Context(64, 32, 64)                 # launches of one batch with the default parameters
+    launches_per_batch = probe.launches_per_compute()
+    probe.close()
     whd = {ci: c.W * c.H * c.D for ci, c in enumerate(cams)}
     sat_whd = sum(len(v) * whd[ci] for ci, v in sat.latencies_ms.items()) / sat.wall_s
     per_cam = [{"shape": [c.W, c.H, c.D], "rate_hz": c.rate_hz, "frames": len(paced.latencies_ms[ci]),
@@ -392,8 +396,8 @@ def run_serve(args, rank, world):
         "e2e": {"value": ss["frames_per_s"], "unit": "frames/s",
                 "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "every request is end to end: host buffers in, host buffers out"},
-        # every batch is one sgmf_compute_batch: 13 kernel launches with the default parameters
-        "gpu_launches": 13 * (paced.stats["batches"] + sat.stats["batches"]), "clocks": clk,
+        # every batch is one sgmf_compute_batch of the default parameters and tuning
+        "gpu_launches": launches_per_batch * (paced.stats["batches"] + sat.stats["batches"]), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -547,6 +551,8 @@ def main():
     ap.add_argument("--mixed-distinct", type=int, default=3,
                     help="distinct generated pairs per shape in the mixed batch (reused cyclically)")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tuning", default=None, metavar="LINE_WARPS,COST_PX,SWEEP",
+                    help="kitti workload: this launch tuning instead of the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank, world, local, pg = dist_setup(args.gpus)
@@ -578,7 +584,10 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
     tuning = None
-    if not args.no_tune:
+    if args.tuning:
+        tuning = tuple(int(v) for v in args.tuning.split(","))
+        sgmf.sgmf_set_tuning(ctx.handle, *tuning)
+    elif not args.no_tune:
         # launch tuning only (results are bit-identical for every candidate)
         tuning, _ = sgmf.sgmf_autotune(ctx.handle, B, dl.data_ptr(), dr.data_ptr(), dli.data_ptr(),
                                        dout.data_ptr(), 2)
@@ -765,7 +774,8 @@ def main():
         "config": {"workload": WORKLOAD, "W": W, "H": H, "D": D, "frames_per_step": B,
                    "batched_launch": True, "l2": "flushed by a 512 MiB write between steps",
                    "lidar": "64 beams, ~5% density", "parallelism": f"replicas x{world}",
-                   "tuning": None if tuning is None else {"line_warps": tuning[0], "cost_px": tuning[1]}},
+                   "tuning": None if tuning is None else {"line_warps": tuning[0], "cost_px": tuning[1],
+                                                         "sweep": tuning[2]}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "latency_single_frame": latency,
         "clocks": clk,

@@ -93,7 +93,11 @@ enum {
     SGMF_STAGE_SUM = 5,      /* uint16 H x W x D: S = sum_r L_r; only after sgmf_set_debug(c, 1) */
     SGMF_STAGE_DSTAR = 6,    /* int16 H x W: d* of Eq. 3 */
     SGMF_STAGE_DPRIME = 7,   /* int16 H x W: d' of the right view (diagonal search) */
-    SGMF_STAGE_DSUB = 8      /* int16 H x W: sub-pixel disparity in 1/16 px; only with subpixel = 1 */
+    SGMF_STAGE_DSUB = 8,     /* int16 H x W: sub-pixel disparity in 1/16 px; only with subpixel = 1 */
+    SGMF_STAGE_BOX_S = 9,    /* uint32 MW x H x W (MW = 2, 4, 6, 8 for D <= 64, 128, 192, 256):
+                                bit d % 32 of word plane d / 32 set when a pixel of the
+                                (2 rs + 1)^2 window (Eq. 5) has d-bar = d; only with semidense */
+    SGMF_STAGE_BOX_C = 10    /* the same with radius rc (Eq. 6); only with a LiDAR check */
 };
 
 /* Fill *p with Table II of the paper (and the documented readings). */
@@ -322,6 +326,16 @@ typedef struct {
                              (each warp walks two lines): 1, 2, 4 (default) or 8 */
     int32_t cost_px;      /* pixels of one row per CTA of the cost kernel: 32, 64 or
                              128 (default) */
+    int32_t sweep;        /* 1: the six vertical and diagonal directions run as two
+                             row-synchronous sweeps of a thread-block cluster per
+                             frame (one launch) instead of the three line kernels
+                             (line_warps is then unused).  0 (default) or 1; 1 needs
+                             the plain (unbanded) method, a row of at most 16 CTAs x
+                             160 pixels (Dp <= 128) or 16 x 80 pixels (Dp > 128) and
+                             a device that can place such a cluster (the context
+                             picks the cluster size that keeps the most CTAs
+                             resident), and is refused otherwise; it takes effect
+                             with 8 paths. */
 } sgmf_tuning;
 
 /* Set / read the context's tuning.  SGMF_ERR_ARG for other values. */
@@ -329,7 +343,8 @@ sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t);
 sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t);
 
 /* Autotuner.  Runs sgmf_compute_batch(c, n, left, right, lidar, out) on the
- * caller's DEVICE frames once per candidate (all 4 x 3 tunings) as a
+ * caller's DEVICE frames once per candidate (the 4 x 3 line-kernel tunings,
+ * and the sweep with each of the 3 cost shapes where it fits) as a
  * warm-up, then `reps` timed runs (CUDA events on the context's stream,
  * 1 <= reps <= 100); keeps the candidate with the smallest median time in
  * the context and returns it in *best and its median in *best_ms (either may

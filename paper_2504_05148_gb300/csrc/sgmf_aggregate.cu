@@ -12,6 +12,10 @@ template <int CPL, bool S8>
 cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 template <int CPL, bool S8>
 cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+template <int CPL>
+cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+template <int CPL>
+int sweep_plan_t(const KParams &k, int nb);
 
 // Dp = 32 * DPL = 16 * CPL
 #define SGMF_DISPATCH(FN, ...)                    \
@@ -29,6 +33,26 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
 
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s) {
   SGMF_DISPATCH(launch_lines_t, k, b, nf, s)
+}
+
+cudaError_t launch_agg_sweep(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  switch (k.DPL) {
+    case 2: return launch_sweep_t<4>(k, b, nf, s);
+    case 4: return launch_sweep_t<8>(k, b, nf, s);
+    case 6: return launch_sweep_t<12>(k, b, nf, s);
+    case 8: return launch_sweep_t<16>(k, b, nf, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int agg_sweep_plan(const KParams &k, int nb) {
+  switch (k.DPL) {
+    case 2: return sweep_plan_t<4>(k, nb);
+    case 4: return sweep_plan_t<8>(k, nb);
+    case 6: return sweep_plan_t<12>(k, nb);
+    case 8: return sweep_plan_t<16>(k, nb);
+    default: return 0;
+  }
 }
 
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s) {

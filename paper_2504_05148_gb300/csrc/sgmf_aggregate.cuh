@@ -639,8 +639,10 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
   const uint8_t *cst = stg + lig * CPL;
   const uint8_t *sst = stg + CF::kCost + lig * CPL * SB;
   // family sums, 2 Dp bytes per pixel: u16 pair sums, or (S8) the down and
-  // up passes' byte vectors
-  const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * (S8 ? 1 : 2);
+  // up passes' byte vectors; NP == 2: the down and up sweeps' u16 sums of
+  // three directions each
+  constexpr bool kPartBytes = S8 && NP != 2;   // byte vectors, else u16 sums
+  const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * (kPartBytes ? 1 : 2);
   for (int t = t_lo; t < t_hi; ++t) {
     const int x = g.fwd ? t - g.delay : g.W - 1 - t;
     const bool valid = x >= 0 && x < g.W;
@@ -679,7 +681,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       uint32_t T[NW];
-      if constexpr (S8) {
+      if constexpr (kPartBytes) {
         const uint32_t z0[CPL / 4] = {};
         uint32_t U[NW];
         unpack_u8<CPL>(pst + j * CF::kPart + r * 2 * Dp, z0, T);         // L_down of the family
@@ -1096,6 +1098,8 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
     return cudaErrorInvalidValue;
   }
   const bool fulld = k.D == k.Dp;
+  if (k.sweep)
+    return fulld ? launch_rows_v<CPL, S8, 2, true, false>(a, nf, s) : launch_rows_v<CPL, S8, 2, false, false>(a, nf, s);
   if (k.num_paths == 8)
     return fulld ? launch_rows_v<CPL, S8, 3, true, false>(a, nf, s) : launch_rows_v<CPL, S8, 3, false, false>(a, nf, s);
   return fulld ? launch_rows_v<CPL, S8, 1, true, false>(a, nf, s) : launch_rows_v<CPL, S8, 1, false, false>(a, nf, s);
@@ -1103,11 +1107,14 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
 
 }  // namespace sgmf
 
-// explicit instantiations of one lane width (CPL cells per lane)
+// explicit instantiations of one lane width (CPL cells per lane); the
+// instantiating file includes sgmf_sweep.cuh
 #define SGMF_AGG_INSTANTIATE(CPL)                                                                        \
   namespace sgmf {                                                                                      \
   template cudaError_t launch_lines_t<CPL, false>(const KParams &, const Buffers &, int, cudaStream_t); \
   template cudaError_t launch_lines_t<CPL, true>(const KParams &, const Buffers &, int, cudaStream_t);  \
   template cudaError_t launch_rows_t<CPL, false>(const KParams &, const Buffers &, int, cudaStream_t);  \
   template cudaError_t launch_rows_t<CPL, true>(const KParams &, const Buffers &, int, cudaStream_t);   \
+  template cudaError_t launch_sweep_t<CPL>(const KParams &, const Buffers &, int, cudaStream_t);         \
+  template int sweep_plan_t<CPL>(const KParams &, int);                                                 \
   }

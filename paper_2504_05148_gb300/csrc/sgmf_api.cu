@@ -27,6 +27,7 @@ struct sgmf_ctx {
   CUtensorMap mapL;   // 64-byte aligned by its declaration
   CUtensorMap mapR;
   bool spill8 = true;
+  bool sweep_ok = false;       // the row-synchronous sweep can run this shape on this device (8 paths)
   size_t bytes = 0;
   std::string err;
   // device staging for sgmf_compute_host
@@ -167,7 +168,7 @@ static void apply_params(sgmf_ctx *c, const sgmf_params &p) {
 
 static void free_all(sgmf_ctx *c) {
   void *ptrs[] = {c->b.imgL, c->b.imgR, c->b.dbar, c->b.dhat, c->b.dstar, c->b.dprime, c->b.dsub, c->b.censL,
-                  c->b.censR, c->b.pres, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
+                  c->b.censR, c->b.boxS, c->b.boxC, c->b.boxTmp, c->b.cost, c->b.part[0],
                   c->b.part[1], c->b.part[2], c->b.spill, c->b.dbg_sum, c->b.band_lo, c->b.err, c->st_left,
                   c->st_right, c->st_lidar, c->st_out};
   for (void *p : ptrs)
@@ -217,6 +218,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   k.pitch = (width + 15) / 16 * 16;
   k.line_warps = 4;
   k.cost_px = 128;
+  k.sweep = 0;
   sgmf_params def;
   sgmf_default_params(&def);
   apply_params(c, def);
@@ -235,10 +237,9 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   A(dalloc(c, &c->b.dsub, n * 2));
   A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censL), n * 8));
   A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censR), n * 8));
-  A(dalloc(c, &c->b.pres, n * 4 * k.MW));
   A(dalloc(c, &c->b.boxS, n * 4 * k.MW));
   A(dalloc(c, &c->b.boxC, n * 4 * k.MW));
-  A(dalloc(c, &c->b.boxTmp, n * 4 * k.MW));
+  A(dalloc(c, &c->b.boxTmp, 2 * n * 4 * k.MW));
   A(dalloc(c, &c->b.cost, nv));
   for (int i = 0; i < 3; ++i) A(dalloc(c, &c->b.part[i], nv * 2));
   A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), 4 * nv * 2));
@@ -261,6 +262,14 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     free_all(c);
     delete c;
     return fail(nullptr, SGMF_ERR_CUDA, "sgmf_create: cuTensorMapEncodeTiled failed");
+  }
+  {
+    // whether the row-synchronous sweep can run this shape (8 paths); the
+    // line kernels stay the default, the sweep is a tuning choice
+    KParams kk = k;
+    kk.num_paths = 8;
+    c->k.sweep_cs = kk.band == 0 ? agg_sweep_plan(kk, c->nb) : 0;
+    c->sweep_ok = c->k.sweep_cs > 0;
   }
   *out = c;
   return SGMF_OK;
@@ -320,11 +329,22 @@ extern "C" sgmf_status sgmf_set_stream(sgmf_ctx *c, void *stream) {
 
 static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STEREO_LIDAR || k.consistency == SGMF_CHECK_LIDAR; }
 
+// the sweep runs when the tuning asks for it and the context allows it
+static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths == 8 && c->sweep_ok; }
+
+// parameters of the aggregation launches: the sweep flag as it will run
+static KParams agg_params(const sgmf_ctx *c) {
+  KParams k = c->k;
+  k.sweep = use_sweep(c) ? 1 : 0;
+  return k;
+}
+
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (!c) return 0;
-  int n = 4 + (c->k.num_paths == 8 ? 3 : 1);   // ingest, census, cost, rows + one line launch per family
-  if (c->k.semidense) n += 3;
-  if (need_boxc(c->k)) n += 2;
+  // ingest, census, cost, rows + one line launch per family (one sweep launch for all six directions)
+  int n = 4 + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1);
+  if (c->k.semidense || need_boxc(c->k)) n += 2;   // box-OR rows and columns, both radii
+  if (c->k.semidense) n += 1;
   n += 1;      // consistency
   if (c->k.band) n += 1;   // band clamp
   return n;
@@ -364,22 +384,26 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
   mark(c, "census");
   LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
+  if (k.semidense || need_boxc(k)) {
+    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end
+    mark(c, "boxor");
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.dbar, c->b.boxTmp, k.semidense ? c->b.boxS : nullptr,
+                               need_boxc(k) ? c->b.boxC : nullptr, s));
+  }
   if (k.semidense) {
-    mark(c, "boxor_semidense");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s));
     mark(c, "semidense");
     LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
   }
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
   mark(c, "agg_lines");
-  LAUNCH_TRY(c, launch_agg_lines(k, c->b, n, c->spill8, s));
+  const KParams ka = agg_params(c);
+  if (ka.sweep)
+    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
+  else
+    LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
   mark(c, "agg_rows_wta");
-  LAUNCH_TRY(c, launch_agg_rows(k, c->b, n, c->spill8, s));
-  if (need_boxc(k)) {
-    mark(c, "boxor_check");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s));
-  }
+  LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
   mark(c, "consistency");
   LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
   mark(c, "end");
@@ -477,8 +501,13 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
     case SGMF_STAGE_CENSUS_L: case SGMF_STAGE_CENSUS_R: need = n * 8; break;
     case SGMF_STAGE_COST: need = n * (k.band ? k.band : k.D); break;
     case SGMF_STAGE_SUM: need = n * (k.band ? k.band : k.D) * 2; break;
+    case SGMF_STAGE_BOX_S: case SGMF_STAGE_BOX_C: need = n * 4 * k.MW; break;
     default: return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: unknown stage %d", stage);
   }
+  if (stage == SGMF_STAGE_BOX_S && !k.semidense)
+    return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: BOX_S needs semidense = 1");
+  if (stage == SGMF_STAGE_BOX_C && !need_boxc(k))
+    return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: BOX_C needs a consistency mode with the LiDAR check");
   if (bytes < need) return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: need %zu bytes, got %zu", need, bytes);
   if (stage == SGMF_STAGE_DSUB && !k.subpixel)
     return fail(c, SGMF_ERR_ARG, "sgmf_debug_stage: DSUB needs subpixel = 1");
@@ -494,6 +523,8 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
     case SGMF_STAGE_DSTAR: CUDA_TRY(c, cudaMemcpy(dst, c->b.dstar, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_DPRIME: CUDA_TRY(c, cudaMemcpy(dst, c->b.dprime, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_DSUB: CUDA_TRY(c, cudaMemcpy(dst, c->b.dsub, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_BOX_S: CUDA_TRY(c, cudaMemcpy(dst, c->b.boxS, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_BOX_C: CUDA_TRY(c, cudaMemcpy(dst, c->b.boxC, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_CENSUS_L:
     case SGMF_STAGE_CENSUS_R: {
       const void *src = stage == SGMF_STAGE_CENSUS_L ? c->b.censL : c->b.censR;
@@ -550,15 +581,20 @@ extern "C" size_t sgmf_device_bytes(const sgmf_ctx *c) { return c ? c->bytes : 0
 // ---- launch tuning -------------------------------------------------------------
 static bool valid_tuning(const sgmf_tuning &t) {
   return (t.line_warps == 1 || t.line_warps == 2 || t.line_warps == 4 || t.line_warps == 8) &&
-         (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128);
+         (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128) && (t.sweep == 0 || t.sweep == 1);
 }
 
 extern "C" sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t) {
   if (!c || !t) return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: NULL argument");
   if (!valid_tuning(*t))
-    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: need line_warps in {1,2,4,8} and cost_px in {32,64,128}");
+    return fail(c, SGMF_ERR_ARG,
+                "sgmf_set_tuning: need line_warps in {1,2,4,8}, cost_px in {32,64,128} and sweep in {0,1}");
+  if (t->sweep && !c->sweep_ok)
+    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: the sweep does not fit this context (banded, or a row wider "
+                                 "than one cluster holds)");
   c->k.line_warps = t->line_warps;
   c->k.cost_px = t->cost_px;
+  c->k.sweep = t->sweep;
   return SGMF_OK;
 }
 
@@ -566,6 +602,7 @@ extern "C" sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t) {
   if (!c || !t) return SGMF_ERR_ARG;
   t->line_warps = c->k.line_warps;
   t->cost_px = c->k.cost_px;
+  t->sweep = c->k.sweep;
   return SGMF_OK;
 }
 
@@ -578,16 +615,19 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
   c->profiling = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   sgmf_status st = SGMF_OK;
-  sgmf_tuning keep{c->k.line_warps, c->k.cost_px}, win = keep;
+  sgmf_tuning keep{c->k.line_warps, c->k.cost_px, c->k.sweep}, win = keep;
   float win_ms = 0.0f;
   bool have = false;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     st = fail(c, SGMF_ERR_CUDA, "sgmf_autotune: cudaEventCreate failed");
   }
+  // the 4 x 3 line-kernel shapes, then the sweep with each cost shape
   const int warps[4] = {1, 2, 4, 8}, pxs[3] = {32, 64, 128};
+  const int ncand = 12 + (c->sweep_ok && c->k.num_paths == 8 ? 3 : 0);
   std::vector<float> t;
-  for (int i = 0; i < 12 && st == SGMF_OK; ++i) {
-    c->k.line_warps = warps[i / 3];
+  for (int i = 0; i < ncand && st == SGMF_OK; ++i) {
+    c->k.sweep = i >= 12;
+    c->k.line_warps = i < 12 ? warps[i / 3] : keep.line_warps;
     c->k.cost_px = pxs[i % 3];
     st = sgmf_compute_batch(c, n, left, right, lidar, out);   // warm-up (and first-use attributes)
     t.clear();
@@ -612,7 +652,7 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
     if (!have || med < win_ms) {
       have = true;
       win_ms = med;
-      win = sgmf_tuning{c->k.line_warps, c->k.cost_px};
+      win = sgmf_tuning{c->k.line_warps, c->k.cost_px, c->k.sweep};
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -621,6 +661,7 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
   const sgmf_tuning chosen = st == SGMF_OK ? win : keep;
   c->k.line_warps = chosen.line_warps;
   c->k.cost_px = chosen.cost_px;
+  c->k.sweep = chosen.sweep;
   if (st != SGMF_OK) return st;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
@@ -642,9 +683,13 @@ extern "C" sgmf_status sgmf_compute_front(sgmf_ctx *c, int n, const uint8_t *lef
   LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
   mark(c, "census");
   LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
+  if (k.semidense || need_boxc(k)) {
+    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end
+    mark(c, "boxor");
+    LAUNCH_TRY(c, launch_boxor(k, n, c->b.dbar, c->b.boxTmp, k.semidense ? c->b.boxS : nullptr,
+                               need_boxc(k) ? c->b.boxC : nullptr, s));
+  }
   if (k.semidense) {
-    mark(c, "boxor_semidense");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxS, k.rs, s));
     mark(c, "semidense");
     LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
   }
@@ -672,13 +717,13 @@ extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
   mark(c, "agg_lines");
-  LAUNCH_TRY(c, launch_agg_lines(k, c->b, n, c->spill8, s));
+  const KParams ka = agg_params(c);
+  if (ka.sweep)
+    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
+  else
+    LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
   mark(c, "agg_rows_wta");
-  LAUNCH_TRY(c, launch_agg_rows(k, c->b, n, c->spill8, s));
-  if (need_boxc(k)) {
-    mark(c, "boxor_check");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.pres, c->b.boxTmp, c->b.boxC, k.rc, s));
-  }
+  LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
   mark(c, "consistency");
   LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
   mark(c, "end");

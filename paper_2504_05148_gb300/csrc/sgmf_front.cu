@@ -1,7 +1,7 @@
 // sgmf_front.cu -- the stages before aggregation (sm_103a):
-//   k_ingest      sparse LiDAR map d-bar + presence masks + pitched image copies
+//   k_ingest      sparse LiDAR map d-bar + pitched image copies
 //   k_census      9x7 census of both images, windows staged in shared memory by TMA
-//   k_boxor_*     separable OR of presence masks over a (2r+1)^2 window
+//   k_boxor_*     OR of the presence masks over (2r+1)^2 windows, both radii
 //   k_semidense   Eq. 5
 //   k_cost        Hamming cost + DDC, Eq. 4, materialised as uint8 [H][W][Dp]
 #include <cuda.h>
@@ -14,8 +14,8 @@ namespace sgmf {
 // --------------------------------------------------------------------------
 // d-bar (Sec. IV: integer sparse disparity aligned with the left view).
 // A LiDAR value f becomes rint(f) (round half to even) when f is finite,
-// f > 0 and rint(f) <= D-1; everything else is invalid (-1).  The presence
-// mask of a pixel has bit d-bar set.  The images are copied into pitched
+// f > 0 and rint(f) <= D-1; everything else is invalid (-1).  (The presence
+// masks, bit d-bar of a pixel, are formed inside the box-OR.)  The images are copied into pitched
 // buffers whose rows start on 16-byte boundaries, as TMA requires.
 __global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b0, const uint8_t *__restrict__ left,
                                                 const uint8_t *__restrict__ right,
@@ -39,9 +39,6 @@ __global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b0, const uin
     }
   }
   b.dbar[p] = (int16_t)v;
-  const size_t plane = (size_t)k.W * k.H;
-  for (int w = 0; w < k.MW; ++w)
-    b.pres[w * plane + p] = (v >= 0 && (v >> 5) == w) ? (1u << (v & 31)) : 0u;
   b.imgL[(size_t)y * k.pitch + x] = left[p];
   b.imgR[(size_t)y * k.pitch + x] = right[p];
 }
@@ -187,97 +184,146 @@ int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch
 }
 
 // --------------------------------------------------------------------------
-// Separable box-OR of presence masks: dst[w][y][x] = OR of src[w][y'][x'] over
-// |x'-x| <= r, |y'-y| <= r inside the image.  The OR over a clipped rectangle
-// is the OR (over rows) of the ORs along each row, so a row pass followed by
-// a column pass is exact.  Each pass builds a doubling table in shared memory
-// (level j holds the OR of 2^j consecutive words); OR being idempotent, the
-// window of L = 2r+1 words is the OR of two level-k entries (2^k <= L < 2^(k+1))
-// that overlap: k + 1 ORs per word instead of L.
-constexpr int kBoxRowTile = 256;
-
-__device__ __forceinline__ int floor_log2(int v) { return 31 - __clz(v); }
-
-__global__ void __launch_bounds__(kBoxRowTile) k_boxor_rows(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-                                                           int W, int H, int r) {
-  extern __shared__ uint32_t seg[];            // two buffers of n words
-  const int y = blockIdx.y, w = blockIdx.z;
-  const size_t base = ((size_t)w * H + y) * W;
-  const int x0 = blockIdx.x * kBoxRowTile;
-  const int n = kBoxRowTile + 2 * r;
-  uint32_t *A = seg, *B = seg + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int x = x0 - r + i;
-    A[i] = (x >= 0 && x < W) ? src[base + x] : 0u;
+// Box-OR of the presence masks (the windows of Eq. 5 and Eq. 6):
+// box[w][y][x] = OR, over the pixels (x', y') with |x'-x| <= r, |y'-y| <= r
+// inside the image whose sparse disparity d = disp(x', y') lies in [0, D),
+// of bit d & 31 of word d >> 5.  The OR over a clipped square is the OR over
+// its rows of the ORs along each row, so a row pass and a column pass make
+// it exactly.  Both radii (r_s of Eq. 5, r_c of Eq. 6) come out of one row
+// pass and one column launch.
+//
+// Row pass, from the sparse map itself: a warp owns 32 consecutive pixels of
+// one row and visits the valid pixels of [x0 - R, x0 + 31 + R] (R the larger
+// radius) 32 at a time: a ballot finds them, a shuffle hands out each one's
+// disparity, and every lane ORs its bit into the words of the radii that
+// reach it.  The work follows the number of valid pixels, not r.
+template <int MW>
+__global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ disp, uint32_t *__restrict__ tmpS,
+                                                   uint32_t *__restrict__ tmpC, int W, int H, int D, int rs,
+                                                   int rc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.y * 8 + warp;
+  if (y >= H) return;                          // warps are independent: no block barrier
+  const int f = blockIdx.z;
+  const int x0 = blockIdx.x * 32, x = x0 + lane;
+  const int16_t *row = disp + ((size_t)f * H + y) * W;
+  const int R = max(rs, rc);                   // an unwanted radius is -1: no pixel is that close
+  uint32_t aS[MW], aC[MW];
+#pragma unroll
+  for (int w = 0; w < MW; ++w) aS[w] = aC[w] = 0u;
+  for (int base = x0 - R; base <= x0 + 31 + R; base += 32) {
+    const int xs = base + lane;
+    const int d = (xs >= 0 && xs < W) ? (int)row[xs] : -1;
+    unsigned m = __ballot_sync(0xffffffffu, d >= 0 && d < D);
+    while (m != 0u) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const int dp = __shfl_sync(0xffffffffu, d, j);
+      const int dx = abs(base + j - x);
+      const uint32_t bit = 1u << (dp & 31);
+      const int ws = dp >> 5;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        const uint32_t add = w == ws ? bit : 0u;
+        if (dx <= rc) aC[w] |= add;
+        if (dx <= rs) aS[w] |= add;
+      }
+    }
   }
-  const int L = 2 * r + 1, k = floor_log2(L);
-  for (int j = 0; j < k; ++j) {
-    __syncthreads();
-    const int s = 1 << j;
-    for (int i = threadIdx.x; i + s < n; i += blockDim.x) B[i] = A[i] | A[i + s];
-    __syncthreads();
-    uint32_t *t = A;
-    A = B;
-    B = t;
-  }
-  __syncthreads();
-  const int x = x0 + threadIdx.x;
   if (x >= W) return;
-  // window [threadIdx.x, threadIdx.x + L - 1] of the segment
-  dst[base + x] = A[threadIdx.x] | A[threadIdx.x + L - (1 << k)];
-}
-
-constexpr int kBoxColW = 32, kBoxColH = 64;
-
-__global__ void __launch_bounds__(256) k_boxor_cols(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-                                                   int W, int H, int r) {
-  extern __shared__ uint32_t blk[];            // two buffers of [(kBoxColH + 2r)][kBoxColW]
-  const int w = blockIdx.z;
-  const size_t plane = (size_t)w * H * W;
-  const int x0 = blockIdx.x * kBoxColW, y0 = blockIdx.y * kBoxColH;
-  const int rows = kBoxColH + 2 * r;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  uint32_t *A = blk, *B = blk + rows * kBoxColW;
-  for (int i = ty; i < rows; i += 8) {
-    const int yy = y0 - r + i, x = x0 + tx;
-    A[i * kBoxColW + tx] = (yy >= 0 && yy < H && x < W) ? src[plane + (size_t)yy * W + x] : 0u;
-  }
-  const int L = 2 * r + 1, k = floor_log2(L);
-  for (int j = 0; j < k; ++j) {
-    __syncthreads();
-    const int s = 1 << j;
-    for (int i = ty; i + s < rows; i += 8) B[i * kBoxColW + tx] = A[i * kBoxColW + tx] | A[(i + s) * kBoxColW + tx];
-    __syncthreads();
-    uint32_t *t = A;
-    A = B;
-    B = t;
-  }
-  __syncthreads();
-  const int x = x0 + tx;
-  if (x >= W) return;
-  const int off = L - (1 << k);
-  for (int oy = ty; oy < kBoxColH; oy += 8) {
-    const int y = y0 + oy;
-    if (y >= H) break;
-    dst[plane + (size_t)y * W + x] = A[oy * kBoxColW + tx] | A[(oy + off) * kBoxColW + tx];
+  const size_t plane = (size_t)H * W, o = (size_t)f * MW * plane + (size_t)y * W + x;
+#pragma unroll
+  for (int w = 0; w < MW; ++w) {
+    if (rs >= 0) tmpS[o + w * plane] = aS[w];
+    if (rc >= 0) tmpC[o + w * plane] = aC[w];
   }
 }
 
-cudaError_t launch_boxor(const KParams &k, int nf, const uint32_t *src, uint32_t *tmp, uint32_t *dst, int radius,
-                         cudaStream_t s) {
-  // frames and mask words are contiguous planes: plane z = f * MW + w
-  dim3 g1((k.W + kBoxRowTile - 1) / kBoxRowTile, k.H, nf * k.MW);
-  size_t sm1 = 2 * (size_t)(kBoxRowTile + 2 * radius) * sizeof(uint32_t);
-  k_boxor_rows<<<g1, kBoxRowTile, sm1, s>>>(src, tmp, k.W, k.H, radius);
+// Column pass (van Herk / Gil-Werman): with the rows cut into blocks of
+// L = 2r + 1, the window [u, u + 2r] is the suffix OR of u's block from u
+// together with the prefix OR of (u + 2r)'s block up to u + 2r, so every
+// output costs O(1) whatever r.  A lane owns one column of kColT output rows;
+// it keeps its kColT + 2r input rows and kColT suffix ORs in shared memory
+// (its own column: no barrier), the 32 lanes of the warp on consecutive x.
+constexpr int kColT = 64;
+
+__host__ __device__ constexpr int boxor_col_smem(int r) { return (2 * kColT + 2 * r) * 32 * 4; }
+
+__global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
+                                                  uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
+                                                  int H, int MW, int rs, int rc) {
+  extern __shared__ uint32_t colbuf[];         // [kColT + 2r][32] inputs, then [kColT][32] suffix ORs
+  const int lane = threadIdx.x;
+  const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
+  const uint32_t *src = which ? tmpC : tmpS;
+  uint32_t *dst = which ? boxC : boxS;
+  const int r = which ? rc : rs;
+  if (r < 0) return;                           // this radius is not wanted
+  const size_t plane = (size_t)H * W, base = ((size_t)f * MW + w) * plane;
+  const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * kColT;
+  const int L = 2 * r + 1, n = kColT + 2 * r;
+  uint32_t *in = colbuf, *suf = colbuf + n * 32;
+  // input row u is image row y0 - r + u (zero outside the image)
+#pragma unroll 8
+  for (int u = 0; u < n; ++u) {
+    const int yy = y0 - r + u;
+    in[u * 32 + lane] = (x < W && yy >= 0 && yy < H) ? src[base + (size_t)yy * W + x] : 0u;
+  }
+  // suffix ORs within the blocks [kL, (k+1)L), for u < kColT: a block end is
+  // at most u + 2r < n
+  uint32_t acc = 0u;
+  int p = (n - 1) % L;                         // position of u in its block
+  for (int u = n - 1; u >= 0; --u) {
+    if (p == L - 1) acc = 0u;
+    acc |= in[u * 32 + lane];
+    if (u < kColT) suf[u * 32 + lane] = acc;
+    p = p == 0 ? L - 1 : p - 1;
+  }
+  // prefix ORs, and out(y0 + u) = suffix(u) | prefix(u + 2r)
+  acc = 0u;
+  p = 0;
+  for (int u = 0; u < n; ++u) {
+    if (p == 0) acc = 0u;
+    acc |= in[u * 32 + lane];
+    const int y = y0 + u - 2 * r;
+    if (u >= 2 * r && x < W && y < H) dst[base + (size_t)y * W + x] = suf[(u - 2 * r) * 32 + lane] | acc;
+    p = p == L - 1 ? 0 : p + 1;
+  }
+}
+
+template <int MW>
+static void launch_boxor_rows(const KParams &k, int nf, const int16_t *disp, uint32_t *tS, uint32_t *tC, int rs,
+                              int rc, cudaStream_t s) {
+  dim3 g((k.W + 31) / 32, (k.H + 7) / 8, nf);
+  k_boxor_rows<MW><<<g, 256, 0, s>>>(disp, tS, tC, k.W, k.H, k.D, rs, rc);
+}
+
+cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
+                         uint32_t *boxC, cudaStream_t s) {
+  const int rs = boxS != nullptr ? k.rs : -1, rc = boxC != nullptr ? k.rc : -1;
+  if (rs < 0 && rc < 0) return cudaSuccess;
+  // the row results: S then C (C alone at tmp when S is not wanted)
+  uint32_t *tS = tmp, *tC = rs >= 0 ? tmp + (size_t)nf * k.MW * k.W * k.H : tmp;
+  switch (k.MW) {
+    case 2: launch_boxor_rows<2>(k, nf, disp, tS, tC, rs, rc, s); break;
+    case 4: launch_boxor_rows<4>(k, nf, disp, tS, tC, rs, rc, s); break;
+    case 6: launch_boxor_rows<6>(k, nf, disp, tS, tC, rs, rc, s); break;
+    case 8: launch_boxor_rows<8>(k, nf, disp, tS, tC, rs, rc, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 g2((k.W + kBoxColW - 1) / kBoxColW, (k.H + kBoxColH - 1) / kBoxColH, nf * k.MW);
-  size_t sm2 = 2 * (size_t)(kBoxColH + 2 * radius) * kBoxColW * sizeof(uint32_t);
-  if (sm2 > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !done[dev]) {
+    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
     if (e != cudaSuccess) return e;
+    done[dev] = true;
   }
-  k_boxor_cols<<<g2, 256, sm2, s>>>(tmp, dst, k.W, k.H, radius);
+  // y: row tile x radius (bit 0), z: frame x word plane
+  dim3 g((k.W + 31) / 32, 2 * ((k.H + kColT - 1) / kColT), nf * k.MW);
+  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
   return cudaGetLastError();
 }
 

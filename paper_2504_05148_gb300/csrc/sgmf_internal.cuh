@@ -4,8 +4,8 @@
 //   images          uint8  [F][H][pitch]   pitched copies (pitch % 16 == 0) for TMA
 //   d-bar, d-hat    int16  [F][H][W]       -1 = invalid
 //   census          u32 (CS 9x7) or u64 (9x7) [F][H][W]
-//   presence masks  u32    [F][MW][H][W]   bit d of word-plane d/32 set when the
-//                                           pixel's (or window's) sparse disparity is d
+//   box-OR masks    u32    [F][MW][H][W]   bit d of word-plane d/32 set when a
+//                                           sparse disparity of the window is d
 //   cost C-bar      uint8  [F][H][W][Dp]   Dp = 32 * DPL >= D, cells d >= D hold 0
 //   partial sums    u16    [F][H][W][Dp]   one per line family (vertical, two diagonals)
 //   spills          uint8/u16 [F][4][line][pos][Dp]  first-direction path costs of a line
@@ -39,6 +39,8 @@ struct KParams {
   int census, semidense, consistency, num_paths, subpixel;
   int nbits;
   int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA
+  int sweep;                  // tuning: 1 = row-synchronous sweep instead of the line kernels
+  int sweep_cs;               // CTAs per sweep cluster (0: the sweep cannot run this context)
   int band;                   // banded mode: band width B (= Dp); 0 = the plain method
   int tw, th;                 // banded mode: band tiles per row / column                  // census bits (31 or 62)
 };
@@ -48,7 +50,8 @@ struct Buffers {   // base pointers of frame 0
   int16_t *dbar, *dhat, *dstar, *dprime;
   int16_t *dsub;              // sub-pixel disparity (1/16 px)
   void *censL, *censR;        // u32 or u64 per pixel
-  uint32_t *pres, *boxS, *boxC, *boxTmp;   // [MW][H][W]
+  uint32_t *boxS, *boxC;      // [MW][H][W] box-ORed presence masks, radii r_s and r_c
+  uint32_t *boxTmp;           // row-pass results of both radii: [2][F][MW][H][W]
   uint8_t *cost;              // [H][W][Dp]
   uint16_t *part[3];          // [H][W][Dp]
   void *spill;                // 4 regions (vertical, diag, anti-diag, rows) of H*W*Dp elements
@@ -76,10 +79,8 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
   const size_t cw = k.census == 1 ? 8 : 4;
   v.censL = static_cast<uint8_t *>(b.censL) + f * px * cw;
   v.censR = static_cast<uint8_t *>(b.censR) + f * px * cw;
-  v.pres = b.pres + f * px * k.MW;
   v.boxS = b.boxS + f * px * k.MW;
   v.boxC = b.boxC + f * px * k.MW;
-  v.boxTmp = b.boxTmp + f * px * k.MW;
   v.cost = b.cost + f * cells;
   for (int i = 0; i < 3; ++i) v.part[i] = b.part[i] + f * cells;
   v.spill = static_cast<uint8_t *>(b.spill) + f * 4 * cells * 2;
@@ -179,12 +180,20 @@ cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint
                           const uint8_t *right, const float *lidar, cudaStream_t s);
 cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
                           cudaStream_t s);
-cudaError_t launch_boxor(const KParams &k, int nf, const uint32_t *src, uint32_t *tmp, uint32_t *dst,
-                         int radius, cudaStream_t s);
+// box-ORs of the presence masks of the sparse map disp [nf][H][W] (values in
+// [0, D) present): radius k.rs into boxS and k.rc into boxC, either may be
+// null; tmp holds nf * MW * H * W words per wanted radius
+cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
+                         uint32_t *boxC, cudaStream_t s);
 cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
+// the six vertical/diagonal directions as two cluster sweeps (k.sweep, clusters of
+// k.sweep_cs CTAs); plan: the cluster size for the context's shape and batch capacity nb on
+// this device, 0 if none
+cudaError_t launch_agg_sweep(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
+int agg_sweep_plan(const KParams &k, int nb);
 cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const int16_t *lo_in, cudaStream_t s);
 cudaError_t launch_cost_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);

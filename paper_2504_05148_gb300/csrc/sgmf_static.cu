@@ -24,19 +24,20 @@
 
 namespace sgmf {
 
-// 8 Mi 32-bit words (32 MiB): three [MW][H][W] mask planes; with D <= 128
-// (MW <= 4) that holds frames of up to about 700 000 pixels.
+// 8 Mi 32-bit words (32 MiB): three [MW][H][W] planes (d-bar in the first,
+// the row-pass results, the box-OR); with D <= 128 (MW <= 4) that holds
+// frames of up to about 700 000 pixels.
 constexpr size_t kStaticScratchWords = size_t(8) << 20;
 static __device__ __align__(256) uint32_t g_check_scratch[kStaticScratchWords];
 
-// presence masks of the raw LiDAR map (the same ingest rule as the pipeline:
-// d-bar = rint(f) for finite f > 0 with rint(f) <= D-1)
-__global__ void __launch_bounds__(256) k_static_presence(int W, int H, int D, int MW, const float *__restrict__ lidar,
-                                                         uint32_t *__restrict__ pres) {
+// d-bar of the raw LiDAR map (the same ingest rule as the pipeline:
+// rint(f) for finite f > 0 with rint(f) <= D-1, else -1)
+__global__ void __launch_bounds__(256) k_static_dbar(int W, int H, int D, const float *__restrict__ lidar,
+                                                     int16_t *__restrict__ dbar) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
-  const size_t p = (size_t)y * W + x, plane = (size_t)W * H;
+  const size_t p = (size_t)y * W + x;
   int v = -1;
   if (lidar != nullptr) {
     const float f = lidar[p];
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(256) k_static_presence(int W, int H, int D, in
       if (r <= (float)(D - 1)) v = (int)r;
     }
   }
-  for (int w = 0; w < MW; ++w) pres[w * plane + p] = (v >= 0 && (v >> 5) == w) ? (1u << (v & 31)) : 0u;
+  dbar[p] = (int16_t)v;
 }
 
 namespace {
@@ -116,12 +117,14 @@ extern "C" sgmf_status sgmf_check_static(int width, int height, int max_disp, co
     return fail_static(SGMF_ERR_CUDA, std::string("sgmf_check_static: cudaGetSymbolAddress failed: ") +
                                           cudaGetErrorString(e));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  uint32_t *pres = scratch, *tmp = scratch + plane, *box = scratch + 2 * plane;
+  // d-bar (int16, the first half plane), the row-pass results, the box-OR
+  int16_t *dbar = reinterpret_cast<int16_t *>(scratch);
+  uint32_t *tmp = scratch + plane, *box = scratch + 2 * plane;
   dim3 grid((width + 31) / 32, (height + 7) / 8);
-  k_static_presence<<<grid, 256, 0, s>>>(width, height, max_disp, k.MW, sparse_lidar_disp, pres);
+  k_static_dbar<<<grid, 256, 0, s>>>(width, height, max_disp, sparse_lidar_disp, dbar);
   e = cudaGetLastError();
   if (e == cudaSuccess && (k.consistency == SGMF_CHECK_STEREO_LIDAR || k.consistency == SGMF_CHECK_LIDAR))
-    e = launch_boxor(k, 1, pres, tmp, box, k.rc, s);
+    e = launch_boxor(k, 1, dbar, tmp, nullptr, box, s);
   if (e == cudaSuccess) {
     Buffers b{};
     b.dstar = const_cast<int16_t *>(dstar);

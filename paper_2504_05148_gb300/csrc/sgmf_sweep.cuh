@@ -1,0 +1,443 @@
+// sgmf_sweep.cuh -- row-synchronous aggregation of the six vertical and
+// diagonal directions of Eq. 2 (Sec. III, 8 paths).
+//
+// The line kernels walk each line of a family separately and read the cost
+// volume once per direction.  Here one thread-block cluster sweeps a whole
+// frame row by row: the down sweep carries r = (0,1), (1,1), (-1,1) together,
+// the up sweep r = (0,-1), (1,-1), (-1,-1), so a sweep reads every cost row
+// once for three directions and writes one u16 sum of the three path costs
+// per cell (the row kernel adds the two sums and its own two directions).
+//
+// A row of the frame is split into strips, one per CTA of the cluster, and a
+// strip into runs of P pixels, one per 16-lane group.  A group keeps the
+// three path-cost vectors of its P pixels in registers.  From one row to the
+// next the vertical direction stays on its pixel, the "from-left" diagonal
+// (predecessor x - 1) moves one pixel right and the "from-right" diagonal
+// (predecessor x + 1) one pixel left, so the only state that crosses a group
+// boundary per row is one vector each way.  Those go through shared-memory
+// slots, double-buffered by row parity.  Inside a CTA a split row barrier (an
+// mbarrier with one arrival per warp) orders them: a group computes the two
+// vectors it sends, waits for the previous row's barrier, reads what entered
+// it, stores what it sends, arrives, and only then does the rest of the row,
+// so the barrier's latency hides behind almost a full row of work.  The
+// strip's end groups exchange with the neighbouring CTAs by st.async, whose
+// bytes complete on the receiving CTA's message barrier; a pair of groups
+// sends its row-t vectors only after receiving the other's row t-1 vectors,
+// which is what makes two slots per direction enough.  No thread waits at
+// cluster scope inside the row loop.
+//
+// Cost rows arrive by bulk copies (one per row and CTA: the strip's pixels
+// are contiguous) into a ring of R stages, two rows ahead.  Every mbarrier
+// wait is bounded (the error word records a timeout); the two cluster
+// barriers, at the start and the end, are executed by every thread.
+#pragma once
+
+#include "sgmf_aggregate.cuh"
+
+namespace sgmf {
+
+struct SweepArgs {
+  KParams k;
+  const uint8_t *cost;
+  uint16_t *sum[2];       // down / up sweep sums, u16 [F][H][W][Dp]
+  int *err;
+  StepConsts sc;
+  int strip;              // pixels per CTA (= 2 * warps * P)
+};
+
+template <int CPL>
+struct SweepCfg {
+  static constexpr int Dp = 16 * CPL, NW = CPL / 2;
+  static constexpr int P = 4;                    // pixels per group
+  // warps per CTA: 20 (96 registers a thread) up to 8 cells per lane, 10 above
+  static constexpr int kMaxWarps = CPL <= 8 ? 20 : 10;
+  static constexpr int kMaxCluster = 16;         // CTAs per cluster (above 8: non-portable)
+  static constexpr int R = 4;                    // ring stages (rows)
+  static constexpr int kSlot = (NW + 1) * 16;    // words of one exchanged vector: NW words + m, per lane
+  // at least kExclusive bytes: one CTA per SM, so that the clusters the
+  // device holds at once are the SMs the sweep occupies
+  static constexpr int kExclusive = 120 * 1024;
+  static constexpr int smem_bytes(int warps) {
+    return max(kExclusive, R * (2 * warps * P) * Dp + (R + 5) * 8 + 2 * 2 * (2 * warps) * kSlot * 4);
+  }
+};
+
+// ---- cluster primitives (inline PTX) -----------------------------------------------
+// The .aligned forms need the whole warp at the same instruction: each call
+// first reconverges the warp.
+__device__ __forceinline__ void cluster_arrive() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// asynchronous 4-byte store into (another CTA's) shared memory whose
+// completion counts 4 bytes on the mbarrier at mbar (same CTA as addr)
+__device__ __forceinline__ void st_async(uint32_t addr, uint32_t v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+               "r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int NW>
+__device__ __forceinline__ void copy_vec(uint32_t (&dst)[NW], const uint32_t (&src)[NW]) {
+#pragma unroll
+  for (int w = 0; w < NW; ++w) dst[w] = src[w];
+}
+
+// one Eq. 2 step from predecessor (L, m) on costs C: the new vector and its min
+template <int NW>
+__device__ __forceinline__ void sweep_step(uint32_t (&out)[NW], uint32_t &mout, const uint32_t (&pred)[NW],
+                                           uint32_t mpred, const uint32_t (&C)[NW], const StepConsts &sc,
+                                           uint32_t edge_lo, uint32_t edge_hi, int grp) {
+  copy_vec<NW>(out, pred);
+  sgm_step<NW>(out, C, mpred, sc, edge_lo, edge_hi);
+  mout = group_min<NW>(out, grp);
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(const __grid_constant__ SweepArgs a) {
+  using CF = SweepCfg<CPL>;
+  constexpr int P = CF::P, NW = CF::NW, Dp = CF::Dp, R = CF::R, SL = CF::kSlot;
+  constexpr uint32_t kMsgBytes = SL * 4;            // one exchanged vector: 16 lanes x (NW + 1) words
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int W = a.k.W, H = a.k.H, strip = a.strip;
+  const int rank = blockIdx.x, ncta = gridDim.x;   // the cluster spans grid.x
+  const bool up = blockIdx.y != 0;
+  const int f = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 4, lig = lane & 15;
+  const int nwarp = blockDim.x >> 5, ng = 2 * nwarp, gi = warp * 2 + grp;
+  const int x_cta = rank * strip;
+  const int npx = min(strip, W - x_cta);           // >= 1: the cluster has ceil(W / strip) CTAs
+  const int xg = x_cta + gi * P;                   // the group's first pixel
+  uint8_t *ring = smem;
+  // mbarriers: R ring stages, the row barrier of the CTA, and the four
+  // message barriers [dir][parity] of the vectors that arrive from the
+  // neighbouring CTAs (dir 0: into group 0 from the left, dir 1: into the
+  // last group from the right)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + R * strip * Dp);
+  uint64_t *rowbar = bars + R;
+  uint64_t *rx = bars + R + 1;
+  uint32_t *slots = reinterpret_cast<uint32_t *>(bars + R + 5);   // [dir][parity][group][NW + 1][16]
+  const size_t fcells = frame_cells(a.k);
+  const uint8_t *cost = a.cost + f * fcells;
+  uint16_t *out = a.sum[up ? 1 : 0] + f * fcells + lig * CPL;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+    mbar_init(rowbar, (uint32_t)nwarp);             // one arrival per warp and row
+    for (int i = 0; i < 4; ++i) mbar_init(&rx[i], 1);   // the receiver's expect_tx arrival
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued = 0;                                  // thread 0: rows whose copy was issued
+  auto issue = [&](int t) {
+    const int y = up ? H - 1 - t : t;
+    mbar_expect_tx(&bars[t % R], (uint32_t)(npx * Dp));
+    bulk_g2s(ring + (size_t)(t % R) * strip * Dp, cost + ((size_t)y * W + x_cta) * Dp, (uint32_t)(npx * Dp),
+             &bars[t % R]);
+    issued = t + 1;
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (H > 1) issue(1);
+  }
+  // every CTA of the cluster runs, its barriers initialised, before the first remote store
+  cluster_arrive();
+  cluster_wait();
+
+  uint32_t z[CPL / 4];
+  pad_bytes<CPL>(a.k.D, lig, z);
+  const uint32_t edge_lo = lig == 0 ? 0xffffffffu : 0u, edge_hi = lig == 15 ? 0xffffffffu : 0u;
+  const StepConsts sc = a.sc;
+  // path-cost vectors of the group's pixels and their minima: vertical,
+  // from-left diagonal (predecessor x - 1), from-right diagonal (x + 1)
+  uint32_t V[P][NW], DL[P][NW], DR[P][NW];
+  uint32_t mV[P], mL[P], mR[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) V[i][w] = DL[i][w] = DR[i][w] = 0u;
+    mV[i] = mL[i] = mR[i] = 0u;
+  }
+  // where this group's two outgoing vectors go: the neighbouring groups'
+  // slots, in this CTA (plain stores) or, for the strip's end groups, in the
+  // neighbouring CTA (st.async, completing on that CTA's message barrier)
+  auto slot = [&](int dir, int par, int g) { return slots + ((dir * 2 + par) * ng + g) * SL + lig; };
+  const bool remote_r = gi == ng - 1, remote_l = gi == 0;
+  const bool send_r = !remote_r || rank + 1 < ncta, send_l = !remote_l || rank > 0;
+  const uint32_t rk_r = remote_r && send_r ? rank + 1 : rank, rk_l = remote_l && send_l ? rank - 1 : rank;
+  const int g_r = remote_r ? 0 : gi + 1, g_l = remote_l ? ng - 1 : gi - 1;
+  const uint32_t dst_r0 = cluster_map(smem_u32(slot(0, 0, g_r)), rk_r);
+  const uint32_t dst_r1 = cluster_map(smem_u32(slot(0, 1, g_r)), rk_r);
+  const uint32_t dst_l0 = cluster_map(smem_u32(slot(1, 0, g_l)), rk_l);
+  const uint32_t dst_l1 = cluster_map(smem_u32(slot(1, 1, g_l)), rk_l);
+  const uint32_t mb_r0 = cluster_map(smem_u32(&rx[0]), rk_r), mb_r1 = cluster_map(smem_u32(&rx[1]), rk_r);
+  const uint32_t mb_l0 = cluster_map(smem_u32(&rx[2]), rk_l), mb_l1 = cluster_map(smem_u32(&rx[3]), rk_l);
+  // vectors that arrive from another CTA: group 0 from the left, the last group from the right
+  const bool recv_l = gi == 0 && rank > 0, recv_r = gi == ng - 1 && rank + 1 < ncta;
+  // path starts at the image border: pixel 0's left predecessor is x = -1
+  // at the strip of x = 0; a pixel's right predecessor x + 1 = W does not exist
+  const uint32_t keep_in_l = xg == 0 ? 0u : 0xffffffffu;
+  bool ok = true;
+  auto bounded = [&](uint64_t *bar, uint32_t parity) {
+    if (!mbar_wait_bounded(bar, parity, kWaitLimit)) {
+      set_error(a.err, kErrTimeout);
+      ok = false;
+    }
+  };
+
+  for (int t = 0; t < H; ++t) {
+    bounded(&bars[t % R], (uint32_t)(t / R) & 1u);
+    const uint8_t *st = ring + (size_t)(t % R) * strip * Dp + gi * P * Dp + lig * CPL;
+    uint32_t C0[NW], CP[NW];
+    unpack_u8<CPL>(st, z, C0);
+    unpack_u8<CPL>(st + (P - 1) * Dp, z, CP);
+    // the two vectors this group sends: from-left of its last pixel (from
+    // its own pixel P-2), from-right of its first pixel (from its pixel 1)
+    uint32_t eL[NW], eR[NW], meL, meR;
+    {
+      const uint32_t kr = xg + 1 < W ? 0xffffffffu : 0u;   // pixel 0's right predecessor inside
+      uint32_t pr[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) pr[w] = DR[1][w] & kr;
+      sweep_step<NW>(eL, meL, DL[P - 2], mL[P - 2], CP, sc, edge_lo, edge_hi, grp);
+      sweep_step<NW>(eR, meR, pr, mR[1] & kr, C0, sc, edge_lo, edge_hi, grp);
+    }
+    // the vectors entering this group from the previous row
+    uint32_t inL[NW], inR[NW], minL = 0u, minR = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) inL[w] = inR[w] = 0u;
+    if (t > 0) {
+      const int par = (t - 1) & 1;
+      // every warp of the CTA has stored row t - 1's vectors (and finished row t - 2)
+      bounded(rowbar, (uint32_t)(t - 1) & 1u);
+      if (recv_l || recv_r) {
+        uint64_t *mb = &rx[(recv_l ? 0 : 1) * 2 + par];
+        if (lig == 0) mbar_expect_tx(mb, kMsgBytes);
+        bounded(mb, (uint32_t)((t - 1) >> 1) & 1u);
+      }
+      const uint32_t *sl = slot(0, par, gi), *sr = slot(1, par, gi);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        inL[w] = sl[w * 16];
+        inR[w] = sr[w * 16];
+      }
+      minL = sl[NW * 16];
+      minR = sr[NW * 16];
+    }
+    // the ring stage of row t - 2 is free: every warp finished that row before its row t - 1 arrival
+    if (threadIdx.x == 0 && issued < H && issued <= t + 2) issue(issued);
+    if (t + 1 < H) {
+      // row t's outgoing vectors (the last row's have no reader)
+      const int par = t & 1;
+      if (send_r) {
+        if (remote_r) {
+          const uint32_t dst = par ? dst_r1 : dst_r0, mb = par ? mb_r1 : mb_r0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eL[w], mb);
+          st_async(dst + NW * 64, meL, mb);
+        } else {
+          uint32_t *d = slot(0, par, g_r);
+#pragma unroll
+          for (int w = 0; w < NW; ++w) d[w * 16] = eL[w];
+          d[NW * 16] = meL;
+        }
+      }
+      if (send_l) {
+        if (remote_l) {
+          const uint32_t dst = par ? dst_l1 : dst_l0, mb = par ? mb_l1 : mb_l0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eR[w], mb);
+          st_async(dst + NW * 64, meR, mb);
+        } else {
+          uint32_t *d = slot(1, par, g_l);
+#pragma unroll
+          for (int w = 0; w < NW; ++w) d[w * 16] = eR[w];
+          d[NW * 16] = meR;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(rowbar);
+    // the rest of the row
+    const uint32_t kl = keep_in_l, kr = xg + P < W ? 0xffffffffu : 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      inL[w] &= kl;
+      inR[w] &= kr;
+    }
+    minL &= kl;
+    minR &= kr;
+    uint32_t carry[NW], mcarry = mL[0];
+    copy_vec<NW>(carry, DL[0]);
+    sweep_step<NW>(DL[0], mL[0], inL, minL, C0, sc, edge_lo, edge_hi, grp);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      uint32_t C[NW];
+      if (i == 0)
+        copy_vec<NW>(C, C0);
+      else if (i == P - 1)
+        copy_vec<NW>(C, CP);
+      else
+        unpack_u8<CPL>(st + i * Dp, z, C);
+      uint32_t mtmp;
+      sweep_step<NW>(V[i], mtmp, V[i], mV[i], C, sc, edge_lo, edge_hi, grp);
+      mV[i] = mtmp;
+      if (i >= 1 && i <= P - 2) {
+        uint32_t nxt[NW];
+        const uint32_t mnxt = mL[i];
+        copy_vec<NW>(nxt, DL[i]);
+        sweep_step<NW>(DL[i], mL[i], carry, mcarry, C, sc, edge_lo, edge_hi, grp);
+        copy_vec<NW>(carry, nxt);
+        mcarry = mnxt;
+        const uint32_t ki = xg + i + 1 < W ? 0xffffffffu : 0u;
+        uint32_t pr[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) pr[w] = DR[i + 1][w] & ki;
+        sweep_step<NW>(DR[i], mR[i], pr, mR[i + 1] & ki, C, sc, edge_lo, edge_hi, grp);
+      } else if (i == 0) {
+        copy_vec<NW>(DR[0], eR);
+        mR[0] = meR;
+      } else {
+        copy_vec<NW>(DL[P - 1], eL);
+        mL[P - 1] = meL;
+        sweep_step<NW>(DR[P - 1], mR[P - 1], inR, minR, C, sc, edge_lo, edge_hi, grp);
+      }
+      const int x = xg + i;
+      if (ok && x < W) {
+        const int y = up ? H - 1 - t : t;
+        uint32_t s[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s[w] = V[i][w] + DL[i][w] + DR[i][w];
+        store_u16<CPL>(out + ((size_t)y * W + x) * Dp, s);
+      }
+    }
+  }
+  // every message was waited for by its receiver; the cluster barrier keeps
+  // every CTA (and its shared memory) alive until all are done
+  cluster_arrive();
+  cluster_wait();
+  if (threadIdx.x == 0 && !ok) {
+    for (int h = max(0, issued - R); h < issued; ++h)
+      mbar_wait_bounded(&bars[h % R], (uint32_t)(h / R) & 1u, kWaitLimit);
+  }
+}
+
+// Warps per CTA when a row of W pixels is split over `ctas` CTAs, or 0 when
+// that split is not allowed (a CTA above kMaxWarps, or an empty last CTA).
+template <int CPL>
+inline int sweep_warps(int W, int ctas) {
+  using CF = SweepCfg<CPL>;
+  if (ctas < 1 || ctas > CF::kMaxCluster) return 0;
+  const int warps = (W + ctas * 2 * CF::P - 1) / (ctas * 2 * CF::P);
+  if (warps > CF::kMaxWarps || (ctas - 1) * 2 * warps * CF::P >= W) return 0;
+  return warps;
+}
+
+template <int CPL>
+static cudaLaunchConfig_t sweep_config(int nf, int ctas, int warps, cudaStream_t s, cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas, 2, nf);
+  cfg.blockDim = dim3(32 * warps);
+  cfg.dynamicSmemBytes = SweepCfg<CPL>::smem_bytes(warps);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// kernel attributes (once per device): the dynamic shared memory and cluster
+// sizes above the portable 8
+template <int CPL>
+static cudaError_t sweep_attributes() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SweepCfg<CPL>::smem_bytes(SweepCfg<CPL>::kMaxWarps));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_agg_sweep<CPL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+// The cluster size (CTAs per cluster) for the sweep of a context that runs
+// up to nb frames per call, or 0 when it cannot run (8 paths and the plain,
+// unbanded method only).  A call is 2 nb cluster jobs of H rows each; with n
+// clusters resident at once it takes ceil(2 nb / n) waves, and a row takes
+// time in proportion to the pixels of one CTA (one CTA per SM).  Among the
+// sizes from the smallest that holds a row up to twice that (at most 16) the
+// one with the fewest waves x pixels per CTA (ties: the smaller cluster).
+template <int CPL>
+int sweep_plan_t(const KParams &k, int nb) {
+  using CF = SweepCfg<CPL>;
+  if (k.num_paths != 8 || k.band != 0) return 0;
+  const int lo = (k.W + 2 * CF::kMaxWarps * CF::P - 1) / (2 * CF::kMaxWarps * CF::P);
+  if (lo > CF::kMaxCluster || sweep_attributes<CPL>() != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int best = 0;
+  long best_cost = 0;
+  for (int cs = lo; cs <= min(CF::kMaxCluster, 2 * lo); ++cs) {
+    const int warps = sweep_warps<CPL>(k.W, cs);
+    if (warps == 0) continue;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = sweep_config<CPL>(1, cs, warps, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_agg_sweep<CPL>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (n < 1) continue;
+    const long cost = (long)((2 * nb + n - 1) / n) * (2 * warps * CF::P);
+    if (best == 0 || cost < best_cost) {
+      best_cost = cost;
+      best = cs;
+    }
+  }
+  return best;
+}
+
+template <int CPL>
+cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  using CF = SweepCfg<CPL>;
+  const int ctas = k.sweep_cs, warps = sweep_warps<CPL>(k.W, ctas);
+  if (warps == 0) return cudaErrorInvalidValue;
+  cudaError_t e = sweep_attributes<CPL>();
+  if (e != cudaSuccess) return e;
+  SweepArgs a;
+  a.k = k;
+  a.cost = b.cost;
+  a.sum[0] = b.part[0];
+  a.sum[1] = b.part[1];
+  a.err = b.err;
+  a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
+  a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
+  a.strip = 2 * warps * CF::P;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = sweep_config<CPL>(nf, ctas, warps, s, attr);
+  return cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL>, a);
+}
+
+}  // namespace sgmf

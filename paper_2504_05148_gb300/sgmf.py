@@ -22,7 +22,8 @@ SGMF_CENSUS_CS9X7, SGMF_CENSUS_9X7 = 0, 1
 SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 0, 1, 2, 3
 BAND_TILE = 8   # banded mode: pixels per side of a band tile (include/sgmf.h)
 (SGMF_STAGE_DBAR, SGMF_STAGE_CENSUS_L, SGMF_STAGE_CENSUS_R, SGMF_STAGE_DHAT, SGMF_STAGE_COST,
- SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME, SGMF_STAGE_DSUB) = range(9)
+ SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME, SGMF_STAGE_DSUB, SGMF_STAGE_BOX_S,
+ SGMF_STAGE_BOX_C) = range(11)
 
 # symbols declared in include/sgmf.h
 EXPORTS = (
@@ -57,7 +58,7 @@ class sgmf_params(ctypes.Structure):
 
 
 class sgmf_tuning(ctypes.Structure):
-    _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32)]
+    _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32), ("sweep", ctypes.c_int32)]
 
 
 class sgmf_server_counters(ctypes.Structure):
@@ -70,6 +71,11 @@ class sgmf_server_counters(ctypes.Structure):
 
 class sgmf_shape(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_disp", ctypes.c_int32)]
+
+
+def mask_words(D: int) -> int:
+    """Word planes of the box-OR masks: Dp / 32 with Dp = 64, 128, 192 or 256."""
+    return 2 if D <= 64 else 4 if D <= 128 else 6 if D <= 192 else 8
 
 
 @dataclass
@@ -380,25 +386,26 @@ def sgmf_bn_tiles(n: int, width: int, height: int, max_disp: int, band: int, con
                                stream or None), None)
 
 
-def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int) -> None:
-    t = sgmf_tuning(line_warps, cost_px)
+def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int, sweep: int = 0) -> None:
+    t = sgmf_tuning(line_warps, cost_px, sweep)
     _check(lib().sgmf_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 
-def sgmf_get_tuning(ctx: int) -> tuple[int, int]:
+def sgmf_get_tuning(ctx: int) -> tuple[int, int, int]:
+    """(line_warps, cost_px, sweep)"""
     t = sgmf_tuning()
     _check(lib().sgmf_get_tuning(ctx, ctypes.byref(t)), ctx)
-    return t.line_warps, t.cost_px
+    return t.line_warps, t.cost_px, t.sweep
 
 
 def sgmf_autotune(ctx: int, n: int, left: int, right: int, lidar: int | None, out: int,
-                  reps: int = 3) -> tuple[tuple[int, int], float]:
-    """Device pointers; returns ((line_warps, cost_px), median ms) of the winner."""
+                  reps: int = 3) -> tuple[tuple[int, int, int], float]:
+    """Device pointers; returns ((line_warps, cost_px, sweep), median ms) of the winner."""
     t = sgmf_tuning()
     ms = ctypes.c_float()
     _check(lib().sgmf_autotune(ctx, n, left, right, lidar or None, out, reps, ctypes.byref(t),
                                ctypes.byref(ms)), ctx)
-    return (t.line_warps, t.cost_px), ms.value
+    return (t.line_warps, t.cost_px, t.sweep), ms.value
 
 
 def sgmf_multi_create(shapes: list[tuple[int, int, int]], params: Params | None = None) -> int:
@@ -422,10 +429,10 @@ def sgmf_multi_classes(m: int) -> int:
     return lib().sgmf_multi_classes(m)
 
 
-def sgmf_multi_class_info(m: int, cls: int) -> tuple[tuple[int, int, int], int, tuple[int, int]]:
+def sgmf_multi_class_info(m: int, cls: int) -> tuple[tuple[int, int, int], int, tuple[int, int, int]]:
     s, n, t = sgmf_shape(), ctypes.c_int(), sgmf_tuning()
     _check(lib().sgmf_multi_class_info(m, cls, ctypes.byref(s), ctypes.byref(n), ctypes.byref(t)), None)
-    return (s.width, s.height, s.max_disp), n.value, (t.line_warps, t.cost_px)
+    return (s.width, s.height, s.max_disp), n.value, (t.line_warps, t.cost_px, t.sweep)
 
 
 def sgmf_multi_autotune(m: int, reps: int = 3) -> None:
@@ -586,6 +593,8 @@ class Context:
             SGMF_STAGE_CENSUS_L: (np.uint64, shape2), SGMF_STAGE_CENSUS_R: (np.uint64, shape2),
             SGMF_STAGE_COST: (np.uint8, shape2 + (self.band or self.D,)),
             SGMF_STAGE_SUM: (np.uint16, shape2 + (self.band or self.D,)),
+            SGMF_STAGE_BOX_S: (np.uint32, (mask_words(self.D),) + shape2),
+            SGMF_STAGE_BOX_C: (np.uint32, (mask_words(self.D),) + shape2),
         }[stage]
         a = np.empty(spec[1], spec[0])
         sgmf_debug_stage(self.handle, stage, a.ctypes.data, a.nbytes)

@@ -52,11 +52,10 @@ def test_default_params_are_table_ii(libpath):
     assert p.subpixel == 0
 
 
-def test_params_struct_matches_header_field_order():
-    """The ctypes mirror lists the header's sgmf_params fields in order (all int32)."""
+def _int32_fields(struct_name):
     import re
     src = open(os.path.join(ROOT, "include", "sgmf.h")).read()
-    body = re.search(r"typedef struct \{(.*?)\} sgmf_params;", src, re.S).group(1)
+    body = re.search(r"typedef struct \{([^{}]*?)\} " + struct_name + ";", src, re.S).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = []
     for decl in body.split(";"):
@@ -65,7 +64,17 @@ def test_params_struct_matches_header_field_order():
             continue
         assert decl.startswith("int32_t "), decl
         names += [n.strip() for n in decl[len("int32_t "):].split(",")]
-    assert [f[0] for f in sgmf.sgmf_params._fields_] == names
+    return names
+
+
+def test_params_struct_matches_header_field_order():
+    """The ctypes mirror lists the header's sgmf_params fields in order (all int32)."""
+    assert [f[0] for f in sgmf.sgmf_params._fields_] == _int32_fields("sgmf_params")
+
+
+def test_tuning_and_shape_structs_match_header():
+    assert [f[0] for f in sgmf.sgmf_tuning._fields_] == _int32_fields("sgmf_tuning")
+    assert [f[0] for f in sgmf.sgmf_shape._fields_] == _int32_fields("sgmf_shape")
 
 
 def test_status_strings(libpath):

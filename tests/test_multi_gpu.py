@@ -15,7 +15,8 @@ from paper_2504_05148_gb300 import sgmf as S
 
 pytestmark = pytest.mark.gpu
 
-TUNINGS = [(w, px) for w in (1, 2, 4, 8) for px in (32, 64, 128)]
+# line kernels with each CTA shape, then the row-synchronous sweep
+TUNINGS = [(w, px, 0) for w in (1, 2, 4, 8) for px in (32, 64, 128)] + [(4, px, 1) for px in (32, 64, 128)]
 
 
 def _run(scene, params, tuning):
@@ -49,18 +50,21 @@ def test_every_tuning_is_bit_exact(gpu, tuning, shape):
 def test_tunings_agree_at_full_size(gpu):
     s = scenes.kitti(2600)
     want = oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out
-    for t in [(2, 32), (8, 128), (4, 64)]:
+    for t in [(2, 32, 0), (8, 128, 0), (4, 64, 1), (4, 128, 1)]:
         np.testing.assert_array_equal(_run(s, S.Params(), t)[0], want, err_msg=str(t))
 
 
 def test_bad_tuning_rejected(gpu):
     ctx = S.Context(64, 32, 32)
     try:
-        for t in [(3, 128), (4, 100), (0, 0), (16, 64), (1, 16)]:
+        assert S.sgmf_get_tuning(ctx.handle) == (4, 128, 0)      # line kernels by default
+        for t in [(3, 128), (4, 100), (0, 0), (16, 64), (1, 16), (4, 128, 2), (4, 128, -1)]:
             with pytest.raises(S.SgmfError) as e:
                 S.sgmf_set_tuning(ctx.handle, *t)
             assert e.value.status == S.SGMF_ERR_ARG
-        assert S.sgmf_get_tuning(ctx.handle) == (4, 128)
+        assert S.sgmf_get_tuning(ctx.handle) == (4, 128, 0)
+        S.sgmf_set_tuning(ctx.handle, 4, 128, 1)                  # the sweep fits this shape
+        assert S.sgmf_get_tuning(ctx.handle) == (4, 128, 1)
     finally:
         ctx.close()
 
@@ -122,7 +126,8 @@ def test_mixed_batch_graph_matches_oracle(gpu):
         for i, s in enumerate(frames2):
             want = oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out
             np.testing.assert_array_equal(m.frame_views(i)[3].cpu().numpy(), want, err_msg=f"replay frame {i}")
-        assert m.launches() == sum(13 for _ in m.classes())
+        # 9 launches per class with the sweep, 11 with the three line kernels
+        assert m.launches() == sum(9 if c[2][2] else 11 for c in m.classes())
 
 
 def test_mixed_batch_autotune_then_replay(gpu):
