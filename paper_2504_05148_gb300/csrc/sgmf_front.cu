@@ -7,6 +7,8 @@
 #include <cuda.h>
 #include <cstdint>
 
+#include <type_traits>
+
 #include "sgmf_internal.cuh"
 
 namespace sgmf {
@@ -242,17 +244,17 @@ __global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ 
 // Column pass (van Herk / Gil-Werman): with the rows cut into blocks of
 // L = 2r + 1, the window [u, u + 2r] is the suffix OR of u's block from u
 // together with the prefix OR of (u + 2r)'s block up to u + 2r, so every
-// output costs O(1) whatever r.  A lane owns one column of kColT output rows;
-// it keeps its kColT + 2r input rows and kColT suffix ORs in shared memory
-// (its own column: no barrier), the 32 lanes of the warp on consecutive x.
+// output costs O(1) whatever r.  A lane owns one column of kColT output rows
+// (the 32 lanes of a warp on consecutive x, so every load is one coalesced
+// row segment) and streams its kColT + 2r input rows twice: backwards for the
+// suffix ORs, which it keeps in shared memory (its own column: no barrier),
+// then forwards for the prefix ORs and the outputs.  The second read hits L2.
 constexpr int kColT = 64;
-
-__host__ __device__ constexpr int boxor_col_smem(int r) { return (2 * kColT + 2 * r) * 32 * 4; }
 
 __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
                                                   uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
                                                   int H, int MW, int rs, int rc) {
-  extern __shared__ uint32_t colbuf[];         // [kColT + 2r][32] inputs, then [kColT][32] suffix ORs
+  __shared__ uint32_t suf[kColT * 32];
   const int lane = threadIdx.x;
   const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
   const uint32_t *src = which ? tmpC : tmpS;
@@ -262,29 +264,29 @@ __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ 
   const size_t plane = (size_t)H * W, base = ((size_t)f * MW + w) * plane;
   const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * kColT;
   const int L = 2 * r + 1, n = kColT + 2 * r;
-  uint32_t *in = colbuf, *suf = colbuf + n * 32;
   // input row u is image row y0 - r + u (zero outside the image)
-#pragma unroll 8
-  for (int u = 0; u < n; ++u) {
+  auto in = [&](int u) -> uint32_t {
     const int yy = y0 - r + u;
-    in[u * 32 + lane] = (x < W && yy >= 0 && yy < H) ? src[base + (size_t)yy * W + x] : 0u;
-  }
-  // suffix ORs within the blocks [kL, (k+1)L), for u < kColT: a block end is
-  // at most u + 2r < n
+    return (x < W && yy >= 0 && yy < H) ? src[base + (size_t)yy * W + x] : 0u;
+  };
+  // suffix ORs within the blocks [kL, (k+1)L) of u, for u < kColT (a block
+  // end is at most u + 2r < n)
   uint32_t acc = 0u;
   int p = (n - 1) % L;                         // position of u in its block
+#pragma unroll 16
   for (int u = n - 1; u >= 0; --u) {
     if (p == L - 1) acc = 0u;
-    acc |= in[u * 32 + lane];
+    acc |= in(u);
     if (u < kColT) suf[u * 32 + lane] = acc;
     p = p == 0 ? L - 1 : p - 1;
   }
   // prefix ORs, and out(y0 + u) = suffix(u) | prefix(u + 2r)
   acc = 0u;
   p = 0;
+#pragma unroll 16
   for (int u = 0; u < n; ++u) {
     if (p == 0) acc = 0u;
-    acc |= in[u * 32 + lane];
+    acc |= in(u);
     const int y = y0 + u - 2 * r;
     if (u >= 2 * r && x < W && y < H) dst[base + (size_t)y * W + x] = suf[(u - 2 * r) * 32 + lane] | acc;
     p = p == L - 1 ? 0 : p + 1;
@@ -313,17 +315,9 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  static bool done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !done[dev]) {
-    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
-    if (e != cudaSuccess) return e;
-    done[dev] = true;
-  }
   // y: row tile x radius (bit 0), z: frame x word plane
   dim3 g((k.W + 31) / 32, 2 * ((k.H + kColT - 1) / kColT), nf * k.MW);
-  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
+  k_boxor_cols<<<g, 32, 0, s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
   return cudaGetLastError();
 }
 
@@ -390,10 +384,45 @@ __device__ __forceinline__ int hamming(CT a, CT b) {
     return __popcll(a ^ b);
 }
 
+// A lane owns DPL consecutive disparities d0 = DPL * lane .. d0 + DPL - 1 of
+// a pixel, whose right-census words cR(x - d) are DPL consecutive entries of
+// the staged window.  They are read as aligned vectors: the window is staged
+// VL times, copy k shifted by k entries, and a pixel reads the copy that
+// puts its run on a vector boundary (lanes DPL entries apart: one vector
+// per lane, no bank conflicts).  The lane packs its cost bytes into words.
+template <typename CT, int DPL>
+struct CostVec {
+  // entries per vector load: 16 bytes, or 8 when DPL is not a multiple of 4 words
+  static constexpr int VL = sizeof(CT) == 8 ? 2 : (DPL % 4 == 0 ? 4 : 2);
+  using V = typename std::conditional<VL * sizeof(CT) == 16, uint4, uint2>::type;
+};
+
+template <int DPL>
+__device__ __forceinline__ void store_cost_bytes(uint8_t *o, const uint32_t (&b)[DPL]) {
+  uint32_t w[(DPL + 3) / 4];
+#pragma unroll
+  for (int j = 0; j < DPL / 4; ++j)
+    w[j] = prmt(prmt(b[4 * j], b[4 * j + 1], 0x1140), prmt(b[4 * j + 2], b[4 * j + 3], 0x1140), 0x5410);
+  if constexpr (DPL == 2) {
+    *reinterpret_cast<uint16_t *>(o) = (uint16_t)prmt(b[0], b[1], 0x1140);
+  } else if constexpr (DPL == 4) {
+    *reinterpret_cast<uint32_t *>(o) = w[0];
+  } else if constexpr (DPL == 6) {   // 2-byte aligned
+    uint16_t *q = reinterpret_cast<uint16_t *>(o);
+    q[0] = (uint16_t)prmt(b[0], b[1], 0x1140);
+    q[1] = (uint16_t)prmt(b[2], b[3], 0x1140);
+    q[2] = (uint16_t)prmt(b[4], b[5], 0x1140);
+  } else {
+    *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+  }
+}
+
 template <typename CT, int DPL, int PX>
 __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
   constexpr int Dp = 32 * DPL;
-  __shared__ CT cr_s[PX + Dp];
+  using CV = CostVec<CT, DPL>;
+  constexpr int VL = CV::VL, NV = DPL / VL, NW = PX + Dp;
+  __shared__ __align__(16) CT cr_s[VL][NW];      // copy k: cr_s[k][i] = cR(base + i + k)
   __shared__ CT cl_s[PX];
   __shared__ int pd_s[PX];
   __shared__ uint8_t tab_s[4 * 64];
@@ -404,10 +433,11 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
-  const int base = x0 - (Dp - 1);               // cr_s[i] = cR(base + i)
-  for (int i = threadIdx.x; i < PX + Dp - 1; i += blockDim.x) {
-    const int xx = base + i;
-    cr_s[i] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
+  const int base = x0 - (Dp - 1);
+  for (int i = threadIdx.x; i < VL * NW; i += blockDim.x) {
+    const int kk = i / NW, j = i % NW;
+    const int xx = base + j + kk;
+    cr_s[kk][j] = (j + kk < PX + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
   }
   if (threadIdx.x < PX) {
     const int xx = x0 + threadIdx.x;
@@ -417,32 +447,54 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   }
   for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
-  // lanes walk disparities (d = lane + 32 j): the right-census reads of a warp
-  // are consecutive words, free of bank conflicts
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d0 = DPL * lane;
   const int npx = min(PX, W - x0);
-  // warp-uniform fast path: every d of the pixel has x - d >= 0, all cells are
-  // real disparities, and without a prior C-bar = H (no table)
+  // every d of every pixel has x - d >= 0 and every cell is a real disparity
   const bool inner = x0 >= Dp - 1 && k.D == Dp;
   for (int px = warp; px < npx; px += 8) {
     const int x = x0 + px;
     const CT c = cl_s[px];
     const int pd = pd_s[px];
-    if (inner && pd < 0) {
+    // cR(x - d) for d = d0 + DPL - 1 - m is entry px + Dp - DPL (lane + 1) + m
+    const int kk = px % VL;
+    const CT *run = &cr_s[kk][px + Dp - DPL * (lane + 1) - kk];
+    CT v[DPL];
 #pragma unroll
-      for (int j = 0; j < DPL; ++j) {
-        const int d = lane + 32 * j;
-        out_s[px * Dp + d] = (uint8_t)hamming<CT>(c, cr_s[px - d + Dp - 1]);
+    for (int q = 0; q < NV; ++q) {
+      const typename CV::V t = reinterpret_cast<const typename CV::V *>(run)[q];
+      const CT *e = reinterpret_cast<const CT *>(&t);
+#pragma unroll
+      for (int m = 0; m < VL; ++m) v[q * VL + m] = e[m];
+    }
+    uint32_t out[DPL];
+    if (inner) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) out[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
+      if (pd >= 0) {
+        // C-bar: the far class for every cell, then the (at most three) cells
+        // with |d - prior| <= 1
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) out[i] = tab_s[2 * 64 + out[i]];
+        const int rel = pd - d0;
+        if (rel >= -1 && rel <= DPL) {
+#pragma unroll
+          for (int i = 0; i < DPL; ++i) {
+            const int dd = abs(i - rel);
+            if (dd <= 1) out[i] = tab_s[dd * 64 + (uint32_t)hamming<CT>(c, v[DPL - 1 - i])];
+          }
+        }
       }
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < DPL; ++j) {
-      const int d = lane + 32 * j;
-      const int h = (x >= d) ? hamming<CT>(c, cr_s[px - d + Dp - 1]) : k.nbits;
-      const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
-      out_s[px * Dp + d] = d < k.D ? tab_s[cls * 64 + h] : (uint8_t)0;
+      for (int i = 0; i < DPL; ++i) {
+        const int d = d0 + i;
+        const int h = x >= d ? hamming<CT>(c, v[DPL - 1 - i]) : k.nbits;
+        const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
+        out[i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
+      }
     }
+    store_cost_bytes<DPL>(out_s + px * Dp + d0, out);
   }
   __syncthreads();
   // the block's [npx][Dp] bytes are contiguous in the cost volume: 16-byte stores
