@@ -222,13 +222,20 @@ __global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ 
       m &= m - 1u;
       const int dp = __shfl_sync(0xffffffffu, d, j);
       const int dx = abs(base + j - x);
-      const uint32_t bit = 1u << (dp & 31);
-      const int ws = dp >> 5;
-#pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        const uint32_t add = w == ws ? bit : 0u;
-        if (dx <= rc) aC[w] |= add;
-        if (dx <= rs) aS[w] |= add;
+      const uint32_t bc = dx <= rc ? 1u << (dp & 31) : 0u, bs = dx <= rs ? 1u << (dp & 31) : 0u;
+      // the point's word plane is the same for the whole warp: a uniform branch
+      switch (dp >> 5) {
+#define SGMF_BOX_ACC(w)      \
+  case w:                    \
+    if constexpr (w < MW) {  \
+      aC[w] |= bc;           \
+      aS[w] |= bs;           \
+    }                        \
+    break;
+        SGMF_BOX_ACC(0) SGMF_BOX_ACC(1) SGMF_BOX_ACC(2) SGMF_BOX_ACC(3)
+        SGMF_BOX_ACC(4) SGMF_BOX_ACC(5) SGMF_BOX_ACC(6) SGMF_BOX_ACC(7)
+#undef SGMF_BOX_ACC
+        default: break;
       }
     }
   }
@@ -244,51 +251,69 @@ __global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ 
 // Column pass (van Herk / Gil-Werman): with the rows cut into blocks of
 // L = 2r + 1, the window [u, u + 2r] is the suffix OR of u's block from u
 // together with the prefix OR of (u + 2r)'s block up to u + 2r, so every
-// output costs O(1) whatever r.  A lane owns one column of kColT output rows
-// (the 32 lanes of a warp on consecutive x, so every load is one coalesced
-// row segment) and streams its kColT + 2r input rows twice: backwards for the
-// suffix ORs, which it keeps in shared memory (its own column: no barrier),
-// then forwards for the prefix ORs and the outputs.  The second read hits L2.
-constexpr int kColT = 64;
+// output costs O(1) whatever r.  A lane owns one column of kColT output rows,
+// the 32 lanes of a warp on consecutive x (every load is one coalesced row
+// segment).  It stages its kColT + 2r input rows in shared memory, many loads
+// in flight, then runs both scans there (its own column: no barrier).
+constexpr int kColT = 32;
+
+__host__ __device__ constexpr int boxor_col_smem(int r) { return (2 * kColT + 2 * r) * 32 * 4; }
 
 __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
                                                   uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
                                                   int H, int MW, int rs, int rc) {
-  __shared__ uint32_t suf[kColT * 32];
+  extern __shared__ uint32_t colbuf[];         // [kColT + 2r][32] inputs, then [kColT][32] suffix ORs
   const int lane = threadIdx.x;
   const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
   const uint32_t *src = which ? tmpC : tmpS;
   uint32_t *dst = which ? boxC : boxS;
   const int r = which ? rc : rs;
   if (r < 0) return;                           // this radius is not wanted
-  const size_t plane = (size_t)H * W, base = ((size_t)f * MW + w) * plane;
+  const size_t base = ((size_t)f * MW + w) * H * W;
   const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * kColT;
-  const int L = 2 * r + 1, n = kColT + 2 * r;
-  // input row u is image row y0 - r + u (zero outside the image)
-  auto in = [&](int u) -> uint32_t {
-    const int yy = y0 - r + u;
-    return (x < W && yy >= 0 && yy < H) ? src[base + (size_t)yy * W + x] : 0u;
-  };
-  // suffix ORs within the blocks [kL, (k+1)L) of u, for u < kColT (a block
-  // end is at most u + 2r < n)
+  const int L = 2 * r + 1, n = kColT + 2 * r, ylo = y0 - r;
+  uint32_t *in = colbuf + lane, *suf = colbuf + n * 32 + lane;
+  // input row u is image row ylo + u, zero outside the image
+  {
+    const int ua = max(0, -ylo), ub = x < W ? min(n, H - ylo) : 0;   // rows inside: [ua, ub)
+    const uint32_t *q = src + base + min(x, W - 1) + (ptrdiff_t)(ylo + ua) * W;
+    for (int u = 0; u < ua; ++u) in[u * 32] = 0u;
+#pragma unroll 16
+    for (int u = ua; u < ub; ++u, q += W) in[u * 32] = *q;
+    for (int u = max(ua, ub); u < n; ++u) in[u * 32] = 0u;
+  }
+  // suffix ORs within the blocks [kL, (k+1)L) of u, kept for u < kColT (a
+  // block end is at most u + 2r < n)
   uint32_t acc = 0u;
   int p = (n - 1) % L;                         // position of u in its block
-#pragma unroll 16
-  for (int u = n - 1; u >= 0; --u) {
+  int u = n - 1;
+  for (; u >= kColT; --u) {
     if (p == L - 1) acc = 0u;
-    acc |= in(u);
-    if (u < kColT) suf[u * 32 + lane] = acc;
+    acc |= in[u * 32];
     p = p == 0 ? L - 1 : p - 1;
   }
-  // prefix ORs, and out(y0 + u) = suffix(u) | prefix(u + 2r)
+#pragma unroll 8
+  for (; u >= 0; --u) {
+    if (p == L - 1) acc = 0u;
+    acc |= in[u * 32];
+    suf[u * 32] = acc;
+    p = p == 0 ? L - 1 : p - 1;
+  }
+  // prefix ORs; out(y0 + i) = suffix(i) | prefix(i + 2r)
   acc = 0u;
   p = 0;
-#pragma unroll 16
-  for (int u = 0; u < n; ++u) {
+  for (u = 0; u < 2 * r; ++u) {
     if (p == 0) acc = 0u;
-    acc |= in(u);
-    const int y = y0 + u - 2 * r;
-    if (u >= 2 * r && x < W && y < H) dst[base + (size_t)y * W + x] = suf[(u - 2 * r) * 32 + lane] | acc;
+    acc |= in[u * 32];
+    p = p == L - 1 ? 0 : p + 1;
+  }
+  const int nout = x < W ? min(kColT, H - y0) : 0;
+  uint32_t *o = dst + base + min(x, W - 1) + (size_t)y0 * W;
+#pragma unroll 8
+  for (int i = 0; i < kColT; ++i, ++u, o += W) {
+    if (p == 0) acc = 0u;
+    acc |= in[u * 32];
+    if (i < nout) *o = suf[i * 32] | acc;
     p = p == L - 1 ? 0 : p + 1;
   }
 }
@@ -315,9 +340,17 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !done[dev]) {
+    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
   // y: row tile x radius (bit 0), z: frame x word plane
   dim3 g((k.W + 31) / 32, 2 * ((k.H + kColT - 1) / kColT), nf * k.MW);
-  k_boxor_cols<<<g, 32, 0, s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
+  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
   return cudaGetLastError();
 }
 
@@ -434,11 +467,12 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
   const int base = x0 - (Dp - 1);
-  for (int i = threadIdx.x; i < VL * NW; i += blockDim.x) {
-    const int kk = i / NW, j = i % NW;
-    const int xx = base + j + kk;
-    cr_s[kk][j] = (j + kk < PX + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
-  }
+#pragma unroll
+  for (int kk = 0; kk < VL; ++kk)
+    for (int j = threadIdx.x; j < NW; j += blockDim.x) {
+      const int xx = base + j + kk;
+      cr_s[kk][j] = (j + kk < PX + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
+    }
   if (threadIdx.x < PX) {
     const int xx = x0 + threadIdx.x;
     const int pd = xx < W ? prior[xx] : -1;
@@ -472,18 +506,10 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
 #pragma unroll
       for (int i = 0; i < DPL; ++i) out[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
       if (pd >= 0) {
-        // C-bar: the far class for every cell, then the (at most three) cells
-        // with |d - prior| <= 1
+        // the far class for every cell; the (at most three) cells with
+        // |d - prior| <= 1 are rewritten after the loop, one thread per pixel
 #pragma unroll
         for (int i = 0; i < DPL; ++i) out[i] = tab_s[2 * 64 + out[i]];
-        const int rel = pd - d0;
-        if (rel >= -1 && rel <= DPL) {
-#pragma unroll
-          for (int i = 0; i < DPL; ++i) {
-            const int dd = abs(i - rel);
-            if (dd <= 1) out[i] = tab_s[dd * 64 + (uint32_t)hamming<CT>(c, v[DPL - 1 - i])];
-          }
-        }
       }
     } else {
 #pragma unroll
@@ -495,6 +521,19 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
       }
     }
     store_cost_bytes<DPL>(out_s + px * Dp + d0, out);
+  }
+  __syncthreads();
+  if (inner && threadIdx.x < npx) {
+    const int px = threadIdx.x, pd = pd_s[px];
+    if (pd >= 0) {
+      const CT c = cl_s[px];
+#pragma unroll
+      for (int j = -1; j <= 1; ++j) {
+        const int d = pd + j;
+        if (d >= 0 && d < Dp)
+          out_s[px * Dp + d] = tab_s[abs(j) * 64 + hamming<CT>(c, cr_s[0][px + Dp - 1 - d])];
+      }
+    }
   }
   __syncthreads();
   // the block's [npx][Dp] bytes are contiguous in the cost volume: 16-byte stores
