@@ -59,12 +59,16 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_kitti_1242x375_d128.txt")
 # ops:   scalar integer operations of the method (Eq. 2: 2 adds of P1, 3 mins,
 #        1 add of C, 1 subtraction of m and 1 min toward the next m = 8 per cell
 #        and direction; the path sum 1 add per cell and direction; WTA 2 mins per cell).
-def algorithmic(name: str, V: int, N: int, num_paths: int = 8):
+def algorithmic(name: str, V: int, N: int, num_paths: int = 8, sweep: bool = False):
     if name == "agg_lines":
+        # the cost volume read once, one byte vector per direction written
         dirs = num_paths - 2
         return {"bytes": V * 1 + (dirs // 2) * 2 * V, "ops": 8 * dirs * V + (dirs // 2) * V}
+    if name == "agg_sweep":
+        # the cost volume read once, two u16 sums of three directions written
+        return {"bytes": V * 1 + 2 * 2 * V, "ops": 8 * 6 * V + 4 * V}
     if name == "agg_rows_wta":
-        fams = (num_paths - 2) // 2
+        fams = 2 if sweep else (num_paths - 2) // 2     # u16 sums (sweep) or byte-vector pairs
         return {"bytes": V * 1 + fams * 2 * V + 4 * N, "ops": 8 * 2 * V + (2 + fams) * V + 2 * V}
     if name == "cost":
         return {"bytes": V + 4 * N * 2 + 2 * N, "ops": 4 * V}
@@ -75,6 +79,7 @@ def algorithmic(name: str, V: int, N: int, num_paths: int = 8):
 # (the shared header and the API file that sizes the buffers go with every one)
 KERNEL_SOURCES = {
     "agg_lines": ("sgmf_aggregate", "sgmf_agg_cpl"),
+    "agg_sweep": ("sgmf_sweep", "sgmf_aggregate", "sgmf_agg_cpl"),
     "agg_rows_wta": ("sgmf_aggregate", "sgmf_agg_cpl"),
     "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor": ("sgmf_front",),
     "semidense": ("sgmf_front",), "cost": ("sgmf_front",),
@@ -535,7 +540,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -692,8 +697,10 @@ def main():
         ctx2.close()
         # single-frame latency: one pair per call, device-timed and host to host
         c1 = sgmf.Context(W, H, D, stream=stream, max_batch=1)
-        if tuning is not None:
-            sgmf.sgmf_set_tuning(c1.handle, *tuning)
+        if not args.no_tune:
+            # one frame per call: its own launch shape (the sweep needs many frames)
+            sgmf.sgmf_autotune(c1.handle, 1, dl.data_ptr(), dr.data_ptr(), dli.data_ptr(), dout.data_ptr(), 2)
+            stream.synchronize()
         dev_ms, host_ms = [], []
         o1 = torch.empty((H, W), dtype=torch.int16, device=dev)
         for it in range(23):
@@ -727,7 +734,7 @@ def main():
     tot = {k: sum(v) for k, v in ktimes.items()}
     dom = max(tot, key=tot.get)
     V, N = W * H * D * B, W * H * B          # every launch covers the B frames of a step
-    alg = algorithmic(dom, V, N)
+    alg = algorithmic(dom, V, N, sweep=tuning is not None and len(tuning) > 2 and tuning[2] == 1)
     sm_mhz = (clk or {}).get("sm_mhz") or peaks["sm_max_mhz"]
     alu_peak = 152 * 64 * 2 * sm_mhz * 1e6       # u16x2 lanes of the ALU pipe, per second
     roof = None

@@ -396,8 +396,8 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   }
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
-  mark(c, "agg_lines");
   const KParams ka = agg_params(c);
+  mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
   if (ka.sweep)
     LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
   else
@@ -716,8 +716,8 @@ extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_
   LAUNCH_TRY(c, launch_band_clamp(k, c->b, n, band_lo, s));
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
-  mark(c, "agg_lines");
   const KParams ka = agg_params(c);
+  mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
   if (ka.sweep)
     LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
   else
