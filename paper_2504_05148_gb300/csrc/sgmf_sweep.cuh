@@ -194,6 +194,8 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
   // path starts at the image border: pixel 0's left predecessor is x = -1
   // at the strip of x = 0; a pixel's right predecessor x + 1 = W does not exist
   const uint32_t keep_in_l = xg == 0 ? 0u : 0xffffffffu;
+  // warps whose groups touch neither border need none of the masks below
+  const bool plain = __all_sync(kFull, xg > 0 && xg + P < W);
   bool ok = true;
   auto bounded = [&](uint64_t *bar, uint32_t parity) {
     if (!mbar_wait_bounded(bar, parity, kWaitLimit)) {
@@ -212,12 +214,16 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
     // its own pixel P-2), from-right of its first pixel (from its pixel 1)
     uint32_t eL[NW], eR[NW], meL, meR;
     {
-      const uint32_t kr = xg + 1 < W ? 0xffffffffu : 0u;   // pixel 0's right predecessor inside
-      uint32_t pr[NW];
+      uint32_t pr[NW], mpr = mR[1];
+      copy_vec<NW>(pr, DR[1]);
+      if (!plain) {
+        const uint32_t kr = xg + 1 < W ? 0xffffffffu : 0u;   // pixel 0's right predecessor inside
 #pragma unroll
-      for (int w = 0; w < NW; ++w) pr[w] = DR[1][w] & kr;
+        for (int w = 0; w < NW; ++w) pr[w] &= kr;
+        mpr &= kr;
+      }
       sweep_step<NW>(eL, meL, DL[P - 2], mL[P - 2], CP, sc, edge_lo, edge_hi, grp);
-      sweep_step<NW>(eR, meR, pr, mR[1] & kr, C0, sc, edge_lo, edge_hi, grp);
+      sweep_step<NW>(eR, meR, pr, mpr, C0, sc, edge_lo, edge_hi, grp);
     }
     // the vectors entering this group from the previous row
     uint32_t inL[NW], inR[NW], minL = 0u, minR = 0u;
@@ -276,14 +282,16 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
     __syncwarp();
     if (lane == 0) mbar_arrive(rowbar);
     // the rest of the row
-    const uint32_t kl = keep_in_l, kr = xg + P < W ? 0xffffffffu : 0u;
+    if (!plain) {
+      const uint32_t kl = keep_in_l, kr = xg + P < W ? 0xffffffffu : 0u;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      inL[w] &= kl;
-      inR[w] &= kr;
+      for (int w = 0; w < NW; ++w) {
+        inL[w] &= kl;
+        inR[w] &= kr;
+      }
+      minL &= kl;
+      minR &= kr;
     }
-    minL &= kl;
-    minR &= kr;
     uint32_t carry[NW], mcarry = mL[0];
     copy_vec<NW>(carry, DL[0]);
     sweep_step<NW>(DL[0], mL[0], inL, minL, C0, sc, edge_lo, edge_hi, grp);
@@ -306,11 +314,15 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
         sweep_step<NW>(DL[i], mL[i], carry, mcarry, C, sc, edge_lo, edge_hi, grp);
         copy_vec<NW>(carry, nxt);
         mcarry = mnxt;
-        const uint32_t ki = xg + i + 1 < W ? 0xffffffffu : 0u;
-        uint32_t pr[NW];
+        uint32_t pr[NW], mpr = mR[i + 1];
+        copy_vec<NW>(pr, DR[i + 1]);
+        if (!plain) {
+          const uint32_t ki = xg + i + 1 < W ? 0xffffffffu : 0u;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) pr[w] = DR[i + 1][w] & ki;
-        sweep_step<NW>(DR[i], mR[i], pr, mR[i + 1] & ki, C, sc, edge_lo, edge_hi, grp);
+          for (int w = 0; w < NW; ++w) pr[w] &= ki;
+          mpr &= ki;
+        }
+        sweep_step<NW>(DR[i], mR[i], pr, mpr, C, sc, edge_lo, edge_hi, grp);
       } else if (i == 0) {
         copy_vec<NW>(DR[0], eR);
         mR[0] = meR;
