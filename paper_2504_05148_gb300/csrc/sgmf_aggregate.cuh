@@ -598,7 +598,7 @@ struct RowArgs {
   int tw, th;
 };
 
-template <int CPL, bool S8>
+template <int CPL, bool S8, int NP>
 struct RowCfg {
   static constexpr int Dp = 16 * CPL;
   static constexpr int K = CPL <= 8 ? 4 : 2;    // walk steps per stage
@@ -607,7 +607,7 @@ struct RowCfg {
   static constexpr int kCost = K * Dp;
   static constexpr int kSpill = K * Dp * SB;
   static constexpr int kPart = K * Dp * 2;
-  static constexpr int kGroup = kCost + kSpill + 3 * kPart;   // per group and stage
+  static constexpr int kGroup = kCost + kSpill + NP * kPart;  // per group and stage: one slot per family buffer
   static constexpr int kStage = 2 * kGroup;
   static constexpr int kSmem = S * kStage + S * 8 + kMaxDisp * 4;
 };
@@ -634,7 +634,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
                                           const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp, int lig,
                                           uint8_t *spill_lane, int16_t *dstar, int16_t *dprime, int16_t *dsub,
                                           uint16_t *dbg_lane, uint32_t *merge, BandState &bs, uint32_t *abuf) {
-  using CF = RowCfg<CPL, S8>;
+  using CF = RowCfg<CPL, S8, NP>;
   constexpr int NW = CPL / 2, Dp = CF::Dp, SB = CF::SB;
   const uint8_t *cst = stg + lig * CPL;
   const uint8_t *sst = stg + CF::kCost + lig * CPL * SB;
@@ -810,7 +810,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
 
 template <int CPL, bool S8, int NP, bool FULLD, bool BANDED>
 __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs a) {
-  using CF = RowCfg<CPL, S8>;
+  using CF = RowCfg<CPL, S8, NP>;
   constexpr int K = CF::K, S = CF::S, Dp = CF::Dp, SB = CF::SB;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * CF::kStage);
@@ -1061,7 +1061,7 @@ cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStrea
 
 template <int CPL, bool S8, int NP, bool FULLD, bool BANDED>
 static cudaError_t launch_rows_v(const RowArgs &a, int nf, cudaStream_t s) {
-  using CF = RowCfg<CPL, S8>;
+  using CF = RowCfg<CPL, S8, NP>;
   // banded: the merge array grows to one word per pixel of the row, followed
   // by the two groups' shift buffers (u16 path costs, u32 accumulators)
   constexpr int kBandMax = CF::kSmem - kMaxDisp * 4 + kMaxDim * 4 + 2 * CF::Dp * 2 + 2 * CF::Dp * 4;
