@@ -274,7 +274,10 @@ sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, const uint16_t 
                          int relu, const uint16_t *mask, uint16_t *y, float *yf, int *err, void *stream);
 
 /* Weight gradient: dw[co][ky][kx][ci] += sum_p dy[p][co] x[p + (ky-1, kx-1)][ci]
- * and db[co] += sum_p dy[p][co] (f32, accumulated: zero them first). */
+ * and db[co] += sum_p dy[p][co] (f32, accumulated: zero them first).  The
+ * sums are deterministic (per-CTA partials added in a fixed order); the
+ * partials live in one library-wide device array, so calls must not overlap
+ * on the GPU. */
 sgmf_status sgmf_bn_wgrad(int n, int h, int w, const uint16_t *x, const uint16_t *dy, float *dw, float *db,
                           int *err, void *stream);
 

@@ -281,16 +281,21 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
 // tiles of 128 (tap, ci) rows x 128 pixels; rows 288..383 stay zero) and B
 // (32 co rows x 128 pixels), issues 3 x 8 MMAs into three 32-column
 // accumulators and waits for them before the next chunk.  The accumulators
-// and the bias gradient are added to dw / db with atomics at the end.
+// and the bias gradient are written as this CTA's partial sums; a second
+// kernel adds the partials of all CTAs in CTA order, so that the gradient
+// (and with it training) does not depend on the order the CTAs finish in.
 constexpr int kWgA = 128 * 128 * 2;     // one A tile: 32 KiB
 constexpr int kWgB = 32 * 128 * 2;      // 8 KiB
 constexpr int kWgSmem = 3 * kWgA + kWgB + 16;
+constexpr int kWgMaxCtas = 304;         // about two CTAs per SM
+constexpr int kWgPart = kBnK * 32 + 32; // one CTA's partial: dw [co][tap][ci], then db [co]
+// partial sums of one sgmf_bn_wgrad call (calls must not overlap on the GPU)
+static __device__ float g_wgrad_part[kWgMaxCtas * kWgPart];
 
 struct BnWgradArgs {
   int n, h, w, chunks;
   const uint16_t *x, *dy;   // bf16 [n][h][w][32]
-  float *dw;                // f32 [co][tap][ci]  (accumulated)
-  float *db;                // f32 [co]           (accumulated)
+  float *part;              // f32 [gridDim.x][kWgPart] partial sums
   int *err;
 };
 
@@ -396,26 +401,34 @@ __global__ void __launch_bounds__(128) k_bn_wgrad(const __grid_constant__ BnWgra
     }
     tc_fence_after();
   }
-  if (ok && issued > 0) {
+  float *part = a.part + (size_t)blockIdx.x * kWgPart;
 #pragma unroll 1
-    for (int t = 0; t < 3; ++t) {
-      float v[32];
+  for (int t = 0; t < 3; ++t) {
+    float v[32];
+    if (ok && issued > 0) {
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * t, v);
-      const int m = 128 * t + warp * 32 + lane;   // (tap, ci) row
-      if (m < kBnK) {
+    } else {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) atomicAdd(&a.dw[c * kBnK + m], v[c]);
-      }
+      for (int c = 0; c < 32; ++c) v[c] = 0.0f;
+    }
+    const int m = 128 * t + warp * 32 + lane;   // (tap, ci) row
+    if (m < kBnK) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) part[c * kBnK + m] = v[c];
     }
   }
+  // bias gradient: each warp's sums, then the four warps in order
+  __shared__ float dbw[4][32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) {
     float s = dbp[c];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && s != 0.0f) atomicAdd(&a.db[c], s);
+    if (lane == 0) dbw[warp][c] = s;
   }
   tc_fence_before();
   __syncthreads();
+  if (threadIdx.x < 32)
+    part[kBnK * 32 + threadIdx.x] = ((dbw[0][threadIdx.x] + dbw[1][threadIdx.x]) + dbw[2][threadIdx.x]) + dbw[3][threadIdx.x];
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
@@ -602,6 +615,18 @@ extern "C" sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, cons
   return bn_launch(cudaGetLastError(), "sgmf_bn_conv");
 }
 
+// dw / db += the partials of `ctas` CTAs, added in CTA order
+__global__ void __launch_bounds__(256) k_bn_wgrad_sum(const float *__restrict__ part, int ctas, float *dw, float *db) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= kWgPart) return;
+  float s = 0.0f;
+  for (int b = 0; b < ctas; ++b) s += part[(size_t)b * kWgPart + o];
+  if (o < kBnK * 32)
+    dw[o] += s;
+  else
+    db[o - kBnK * 32] += s;
+}
+
 extern "C" sgmf_status sgmf_bn_wgrad(int n, int h, int w, const uint16_t *x, const uint16_t *dy, float *dw, float *db,
                                      int *err, void *stream) {
   if (n < 1 || h < 1 || w < 1 || !x || !dy || !dw || !db || !err) return SGMF_ERR_ARG;
@@ -615,10 +640,17 @@ extern "C" sgmf_status sgmf_bn_wgrad(int n, int h, int w, const uint16_t *x, con
   }
   const long long P = (long long)n * h * w;
   const long long nchunk = (P + 127) / 128;
-  const int chunks = (int)((nchunk + 303) / 304);          // about two CTAs per SM
-  const unsigned grid = (unsigned)((nchunk + chunks - 1) / chunks);
-  BnWgradArgs a{n, h, w, chunks, x, dy, dw, db, err};
-  k_bn_wgrad<<<grid, 128, kWgSmem, static_cast<cudaStream_t>(stream)>>>(a);
+  const int chunks = (int)((nchunk + kWgMaxCtas - 1) / kWgMaxCtas);
+  const unsigned grid = (unsigned)((nchunk + chunks - 1) / chunks);   // <= kWgMaxCtas
+  float *part = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&part), g_wgrad_part);
+  if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_wgrad scratch");
+  BnWgradArgs a{n, h, w, chunks, x, dy, part, err};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_bn_wgrad<<<grid, 128, kWgSmem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_wgrad");
+  k_bn_wgrad_sum<<<(kWgPart + 255) / 256, 256, 0, s>>>(part, (int)grid, dw, db);
   return bn_launch(cudaGetLastError(), "sgmf_bn_wgrad");
 }
 
