@@ -595,7 +595,7 @@ def main():
     elif not args.no_tune:
         # launch tuning only (results are bit-identical for every candidate)
         tuning, _ = sgmf.sgmf_autotune(ctx.handle, B, dl.data_ptr(), dr.data_ptr(), dli.data_ptr(),
-                                       dout.data_ptr(), 2)
+                                       dout.data_ptr(), 5)
         stream.synchronize()
 
     def step():

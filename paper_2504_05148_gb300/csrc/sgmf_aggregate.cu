@@ -15,7 +15,7 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
 template <int CPL>
 cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 template <int CPL>
-int sweep_plan_t(const KParams &k, int nb);
+int sweep_plan_t(const KParams &k, int nb, int *slots);
 
 // Dp = 32 * DPL = 16 * CPL
 #define SGMF_DISPATCH(FN, ...)                    \
@@ -45,12 +45,12 @@ cudaError_t launch_agg_sweep(const KParams &k, const Buffers &b, int nf, cudaStr
   }
 }
 
-int agg_sweep_plan(const KParams &k, int nb) {
+int agg_sweep_plan(const KParams &k, int nb, int *slots) {
   switch (k.DPL) {
-    case 2: return sweep_plan_t<4>(k, nb);
-    case 4: return sweep_plan_t<8>(k, nb);
-    case 6: return sweep_plan_t<12>(k, nb);
-    case 8: return sweep_plan_t<16>(k, nb);
+    case 2: return sweep_plan_t<4>(k, nb, slots);
+    case 4: return sweep_plan_t<8>(k, nb, slots);
+    case 6: return sweep_plan_t<12>(k, nb, slots);
+    case 8: return sweep_plan_t<16>(k, nb, slots);
     default: return 0;
   }
 }

@@ -1116,5 +1116,5 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
   template cudaError_t launch_rows_t<CPL, false>(const KParams &, const Buffers &, int, cudaStream_t);  \
   template cudaError_t launch_rows_t<CPL, true>(const KParams &, const Buffers &, int, cudaStream_t);   \
   template cudaError_t launch_sweep_t<CPL>(const KParams &, const Buffers &, int, cudaStream_t);         \
-  template int sweep_plan_t<CPL>(const KParams &, int);                                                 \
+  template int sweep_plan_t<CPL>(const KParams &, int, int *);                                          \
   }

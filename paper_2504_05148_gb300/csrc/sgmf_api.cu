@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -28,6 +29,11 @@ struct sgmf_ctx {
   CUtensorMap mapR;
   bool spill8 = true;
   bool sweep_ok = false;       // the row-synchronous sweep can run this shape on this device (8 paths)
+  int sweep_slots = 0;         // sweep clusters the device holds at once
+  // with the sweep, the first part of a batch runs its row kernel on this
+  // second stream while the rest of the batch is in the sweep
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_part = nullptr, ev_rows = nullptr;
   size_t bytes = 0;
   std::string err;
   // device staging for sgmf_compute_host
@@ -175,6 +181,11 @@ static void free_all(sgmf_ctx *c) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
+  if (c->ev_part) cudaEventDestroy(c->ev_part);
+  if (c->ev_rows) cudaEventDestroy(c->ev_rows);
+  if (c->side) cudaStreamDestroy(c->side);
+  c->ev_part = c->ev_rows = nullptr;
+  c->side = nullptr;
 }
 
 template <typename T>
@@ -268,8 +279,15 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     // line kernels stay the default, the sweep is a tuning choice
     KParams kk = k;
     kk.num_paths = 8;
-    c->k.sweep_cs = kk.band == 0 ? agg_sweep_plan(kk, c->nb) : 0;
+    c->k.sweep_cs = kk.band == 0 ? agg_sweep_plan(kk, c->nb, &c->sweep_slots) : 0;
     c->sweep_ok = c->k.sweep_cs > 0;
+    if (c->sweep_ok && c->nb >= 2 &&
+        (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_part, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      c->sweep_slots = 0;        // no split: everything on the context's stream
+    }
   }
   *out = c;
   return SGMF_OK;
@@ -332,6 +350,20 @@ static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STE
 // the sweep runs when the tuning asks for it and the context allows it
 static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths == 8 && c->sweep_ok; }
 
+// Frames of the first part when a sweep batch of n frames is split (0: no
+// split).  The first part's row kernel runs on the side stream beside the
+// rest's sweep, filling the SMs the sweep clusters leave; the first part is
+// a whole number of sweep waves (2 n1 cluster jobs a multiple of the
+// resident clusters), so the split adds no wave.  Closest to n / 2.
+static int sweep_split(const sgmf_ctx *c, int n) {
+  if (!c->side || c->sweep_slots < 1 || n < 2) return 0;
+  const int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 n1 % slots == 0
+  int best = 0;
+  for (int n1 = m; n1 < n; n1 += m)
+    if (best == 0 || abs(2 * n1 - n) < abs(2 * best - n)) best = n1;
+  return best;
+}
+
 // parameters of the aggregation launches: the sweep flag as it will run
 static KParams agg_params(const sgmf_ctx *c) {
   KParams k = c->k;
@@ -342,7 +374,9 @@ static KParams agg_params(const sgmf_ctx *c) {
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (!c) return 0;
   // ingest, census, cost, rows + one line launch per family (one sweep launch for all six directions)
+  // (a split sweep batch launches the sweep and the row kernel twice; counted for a full batch)
   int n = 4 + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1);
+  if (use_sweep(c) && sweep_split(c, c->nb) > 0) n += 2;
   if (c->k.semidense || need_boxc(c->k)) n += 2;   // box-OR rows and columns, both radii
   if (c->k.semidense) n += 1;
   n += 1;      // consistency
@@ -397,13 +431,29 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
   const KParams ka = agg_params(c);
+  const int n1 = ka.sweep ? sweep_split(c, n) : 0;
   mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
-  if (ka.sweep)
-    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
-  else
-    LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
-  mark(c, "agg_rows_wta");
-  LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
+  if (n1 > 0) {
+    // frames [0, n1) through the sweep, then [n1, n) through the sweep while
+    // [0, n1) go through the row kernel on the side stream
+    const Buffers b1 = frame_view(k, c->b, n1);
+    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n1, s));
+    CUDA_TRY(c, cudaEventRecord(c->ev_part, s));
+    LAUNCH_TRY(c, launch_agg_sweep(ka, b1, n - n1, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part, 0));
+    LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n1, c->spill8, c->side));
+    CUDA_TRY(c, cudaEventRecord(c->ev_rows, c->side));
+    mark(c, "agg_rows_wta");
+    LAUNCH_TRY(c, launch_agg_rows(ka, b1, n - n1, c->spill8, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_rows, 0));
+  } else {
+    if (ka.sweep)
+      LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
+    else
+      LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
+    mark(c, "agg_rows_wta");
+    LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
+  }
   mark(c, "consistency");
   LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
   mark(c, "end");

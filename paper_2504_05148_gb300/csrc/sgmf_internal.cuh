@@ -191,9 +191,9 @@ cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool sp
 cudaError_t launch_agg_rows(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);
 // the six vertical/diagonal directions as two cluster sweeps (k.sweep, clusters of
 // k.sweep_cs CTAs); plan: the cluster size for the context's shape and batch capacity nb on
-// this device, 0 if none
+// this device, 0 if none, and in *slots the number of such clusters the device holds at once
 cudaError_t launch_agg_sweep(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
-int agg_sweep_plan(const KParams &k, int nb);
+int agg_sweep_plan(const KParams &k, int nb, int *slots);
 cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const int16_t *lo_in, cudaStream_t s);
 cudaError_t launch_cost_banded(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_consistency(const KParams &k, const Buffers &b, int nf, int16_t *out, cudaStream_t s);

@@ -401,7 +401,7 @@ static cudaError_t sweep_attributes() {
 // sizes from the smallest that holds a row up to twice that (at most 16) the
 // one with the fewest waves x pixels per CTA (ties: the smaller cluster).
 template <int CPL>
-int sweep_plan_t(const KParams &k, int nb) {
+int sweep_plan_t(const KParams &k, int nb, int *slots) {
   using CF = SweepCfg<CPL>;
   if (k.num_paths != 8 || k.band != 0) return 0;
   const int lo = (k.W + 2 * CF::kMaxWarps * CF::P - 1) / (2 * CF::kMaxWarps * CF::P);
@@ -409,7 +409,7 @@ int sweep_plan_t(const KParams &k, int nb) {
     cudaGetLastError();
     return 0;
   }
-  int best = 0;
+  int best = 0, best_n = 0;
   long best_cost = 0;
   for (int cs = lo; cs <= min(CF::kMaxCluster, 2 * lo); ++cs) {
     const int warps = sweep_warps<CPL>(k.W, cs);
@@ -426,8 +426,10 @@ int sweep_plan_t(const KParams &k, int nb) {
     if (best == 0 || cost < best_cost) {
       best_cost = cost;
       best = cs;
+      best_n = n;
     }
   }
+  if (slots != nullptr) *slots = best_n;
   return best;
 }
 

@@ -126,3 +126,30 @@ def test_sweep_refused_where_it_does_not_fit(gpu):
             S.sgmf_set_tuning(h, 4, 128, 1)
     finally:
         S.sgmf_destroy(h)
+
+
+def test_split_batch_matches_oracle(gpu):
+    """16 frames of a 1242-pixel row: the batch splits into a first part of
+    whole sweep waves, whose row kernel runs on the second stream beside the
+    rest's sweep; every frame must equal the oracle, and the result must not
+    depend on the split (a one-frame context gives the same output)."""
+    import torch
+    dev = torch.device("cuda:0")
+    W, H, D, n = 1242, 10, 128, 16
+    scs = [scenes.random_small(9800 + i, W, H, D) for i in range(n)]
+    ctx = S.Context(W, H, D, max_batch=n)
+    try:
+        S.sgmf_set_tuning(ctx.handle, 4, 128, 1)
+        out = torch.empty((n, H, W), dtype=torch.int16, device=dev)
+        for _ in range(2):                 # twice: the events and the second stream are reused
+            out.fill_(-7)
+            ctx.compute(torch.from_numpy(np.stack([s.left for s in scs])).to(dev),
+                        torch.from_numpy(np.stack([s.right for s in scs])).to(dev),
+                        torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev), out)
+            ctx.sync()
+        got = out.cpu().numpy()
+    finally:
+        ctx.close()
+    for i, s in enumerate(scs):
+        np.testing.assert_array_equal(got[i], oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out,
+                                      err_msg=f"frame {i}")
