@@ -348,8 +348,9 @@ sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t);
 /* Autotuner.  Runs sgmf_compute_batch(c, n, left, right, lidar, out) on the
  * caller's DEVICE frames once per candidate (the 4 x 3 line-kernel tunings,
  * and the sweep with each of the 3 cost shapes where it fits) as a
- * warm-up, then `reps` timed runs (CUDA events on the context's stream,
- * 1 <= reps <= 100); keeps the candidate with the smallest median time in
+ * warm-up, then `reps` timed runs, each after overwriting up to 256 MiB of
+ * the context's scratch so that it starts with a cold L2 (CUDA events on the
+ * context's stream, 1 <= reps <= 100); keeps the candidate with the smallest median time in
  * the context and returns it in *best and its median in *best_ms (either may
  * be NULL).  Synchronises the stream; out receives the (identical) output. */
 sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right, const float *lidar,

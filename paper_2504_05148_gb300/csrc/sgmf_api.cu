@@ -30,10 +30,13 @@ struct sgmf_ctx {
   bool spill8 = true;
   bool sweep_ok = false;       // the row-synchronous sweep can run this shape on this device (8 paths)
   int sweep_slots = 0;         // sweep clusters the device holds at once
-  // with the sweep, the first part of a batch runs its row kernel on this
-  // second stream while the rest of the batch is in the sweep
+  size_t spill_bytes = 0;
+  // with the sweep, a batch goes through in parts: each part's row kernel
+  // runs on this second stream while the next part is in the sweep
+  static constexpr int kMaxParts = 8;
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_part = nullptr, ev_rows = nullptr;
+  cudaEvent_t ev_part[kMaxParts] = {};
+  cudaEvent_t ev_rows = nullptr;
   size_t bytes = 0;
   std::string err;
   // device staging for sgmf_compute_host
@@ -181,10 +184,13 @@ static void free_all(sgmf_ctx *c) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
-  if (c->ev_part) cudaEventDestroy(c->ev_part);
+  for (cudaEvent_t &e : c->ev_part) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   if (c->ev_rows) cudaEventDestroy(c->ev_rows);
   if (c->side) cudaStreamDestroy(c->side);
-  c->ev_part = c->ev_rows = nullptr;
+  c->ev_rows = nullptr;
   c->side = nullptr;
 }
 
@@ -253,7 +259,8 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   A(dalloc(c, &c->b.boxTmp, 2 * n * 4 * k.MW));
   A(dalloc(c, &c->b.cost, nv));
   for (int i = 0; i < 3; ++i) A(dalloc(c, &c->b.part[i], nv * 2));
-  A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), 4 * nv * 2));
+  c->spill_bytes = 4 * nv * 2;
+  A(dalloc(c, reinterpret_cast<uint16_t **>(&c->b.spill), c->spill_bytes));
   if (band) {
     A(dalloc(c, &c->b.band_lo, (size_t)k.tw * k.th * max_batch * 2));
   }
@@ -281,12 +288,14 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     kk.num_paths = 8;
     c->k.sweep_cs = kk.band == 0 ? agg_sweep_plan(kk, c->nb, &c->sweep_slots) : 0;
     c->sweep_ok = c->k.sweep_cs > 0;
-    if (c->sweep_ok && c->nb >= 2 &&
-        (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-         cudaEventCreateWithFlags(&c->ev_part, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) != cudaSuccess)) {
+    bool ok = !(c->sweep_ok && c->nb >= 2) ||
+              (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) == cudaSuccess);
+    for (int i = 0; ok && c->side && i < sgmf_ctx::kMaxParts; ++i)
+      ok = cudaEventCreateWithFlags(&c->ev_part[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
       cudaGetLastError();
-      c->sweep_slots = 0;        // no split: everything on the context's stream
+      c->sweep_slots = 0;        // no parts: everything on the context's stream
     }
   }
   *out = c;
@@ -350,18 +359,18 @@ static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STE
 // the sweep runs when the tuning asks for it and the context allows it
 static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths == 8 && c->sweep_ok; }
 
-// Frames of the first part when a sweep batch of n frames is split (0: no
-// split).  The first part's row kernel runs on the side stream beside the
-// rest's sweep, filling the SMs the sweep clusters leave; the first part is
-// a whole number of sweep waves (2 n1 cluster jobs a multiple of the
-// resident clusters), so the split adds no wave.  Closest to n / 2.
-static int sweep_split(const sgmf_ctx *c, int n) {
+// Frames per part when a sweep batch of n frames goes through in parts (0:
+// one part).  A part's row kernel runs on the side stream beside the next
+// part's sweep, filling the SMs (and the register room) the sweep clusters
+// leave.  Every part but the last is one wave of sweep clusters (2 m
+// cluster jobs, the resident count or its smallest even multiple), so the
+// parts add no wave; at most kMaxParts parts.
+static int sweep_part(const sgmf_ctx *c, int n) {
   if (!c->side || c->sweep_slots < 1 || n < 2) return 0;
-  const int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 n1 % slots == 0
-  int best = 0;
-  for (int n1 = m; n1 < n; n1 += m)
-    if (best == 0 || abs(2 * n1 - n) < abs(2 * best - n)) best = n1;
-  return best;
+  int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 m % slots == 0
+  if (m >= n) return 0;
+  while ((n + m - 1) / m > sgmf_ctx::kMaxParts) m *= 2;
+  return m;
 }
 
 // parameters of the aggregation launches: the sweep flag as it will run
@@ -374,9 +383,12 @@ static KParams agg_params(const sgmf_ctx *c) {
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (!c) return 0;
   // ingest, census, cost, rows + one line launch per family (one sweep launch for all six directions)
-  // (a split sweep batch launches the sweep and the row kernel twice; counted for a full batch)
+  // (a sweep batch in parts launches the sweep and the row kernel once per part; counted for a full batch)
   int n = 4 + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1);
-  if (use_sweep(c) && sweep_split(c, c->nb) > 0) n += 2;
+  if (use_sweep(c) && sweep_part(c, c->nb) > 0) {
+    const int m = sweep_part(c, c->nb), parts = (c->nb + m - 1) / m;
+    n += 2 * (parts - 1);
+  }
   if (c->k.semidense || need_boxc(c->k)) n += 2;   // box-OR rows and columns, both radii
   if (c->k.semidense) n += 1;
   n += 1;      // consistency
@@ -431,20 +443,22 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   mark(c, "cost");
   LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
   const KParams ka = agg_params(c);
-  const int n1 = ka.sweep ? sweep_split(c, n) : 0;
+  const int m = ka.sweep ? sweep_part(c, n) : 0;
   mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
-  if (n1 > 0) {
-    // frames [0, n1) through the sweep, then [n1, n) through the sweep while
-    // [0, n1) go through the row kernel on the side stream
-    const Buffers b1 = frame_view(k, c->b, n1);
-    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n1, s));
-    CUDA_TRY(c, cudaEventRecord(c->ev_part, s));
-    LAUNCH_TRY(c, launch_agg_sweep(ka, b1, n - n1, s));
-    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part, 0));
-    LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n1, c->spill8, c->side));
+  if (m > 0) {
+    // part i: frames [i m, min(n, (i + 1) m)) through the sweep on the
+    // context's stream, then through the row kernel on the side stream
+    // while part i + 1 is in the sweep
+    for (int i = 0, f0 = 0; f0 < n; ++i, f0 += m) {
+      const int nf = std::min(m, n - f0);
+      const Buffers bp = frame_view(k, c->b, f0);
+      LAUNCH_TRY(c, launch_agg_sweep(ka, bp, nf, s));
+      CUDA_TRY(c, cudaEventRecord(c->ev_part[i], s));
+      CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part[i], 0));
+      LAUNCH_TRY(c, launch_agg_rows(ka, bp, nf, c->spill8, c->side));
+    }
     CUDA_TRY(c, cudaEventRecord(c->ev_rows, c->side));
     mark(c, "agg_rows_wta");
-    LAUNCH_TRY(c, launch_agg_rows(ka, b1, n - n1, c->spill8, s));
     CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_rows, 0));
   } else {
     if (ka.sweep)
@@ -682,6 +696,9 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
     st = sgmf_compute_batch(c, n, left, right, lidar, out);   // warm-up (and first-use attributes)
     t.clear();
     for (int r = 0; r < reps && st == SGMF_OK; ++r) {
+      // start each timed run with a cold L2, as a stream of batches finds it:
+      // overwrite part of the spill scratch (rewritten by every compute anyway)
+      cudaMemsetAsync(c->b.spill, 0, std::min(c->spill_bytes, (size_t)256 << 20), c->stream);
       cudaEventRecord(e0, c->stream);
       st = sgmf_compute_batch(c, n, left, right, lidar, out);
       cudaEventRecord(e1, c->stream);
