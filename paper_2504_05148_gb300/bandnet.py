@@ -256,12 +256,19 @@ class LearnedSGM:
     per-frame fallback."""
 
     def __init__(self, W: int, H: int, D: int, net: BandNet, band: int = 64, params=None, max_batch: int = 1,
-                 conf_min: float = 0.5, fallback_frac: float = 0.02):
+                 conf_min: float = 0.5, fallback_frac: float = 0.02, sweep: bool | None = None):
         import torch
         self.W, self.H, self.D, self.band = W, H, D, band
         self.net = net
         self.conf_min, self.fallback_frac = conf_min, fallback_frac
         self.banded = S.Context(W, H, D, params, band=band, max_batch=max_batch)
+        # the cluster sweep for the banded walks where it fits; it needs several
+        # frames per call to fill the GPU (one cluster per frame and direction)
+        if sweep if sweep is not None else max_batch >= 4:
+            try:
+                S.sgmf_set_tuning(self.banded.handle, 4, 128, 1)
+            except S.SgmfError:
+                pass
         self.plain = S.Context(W, H, D, params, max_batch=max_batch)
         dev = torch.device("cuda")
         self.H4, self.W4 = _q(4, H), _q(4, W)

@@ -1092,6 +1092,7 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
   a.th = k.th;
   if (k.band) {
     if constexpr (CPL <= 8) {
+      if (k.sweep) return launch_rows_v<CPL, S8, 2, true, true>(a, nf, s);
       if (k.num_paths == 8) return launch_rows_v<CPL, S8, 3, true, true>(a, nf, s);
       return launch_rows_v<CPL, S8, 1, true, true>(a, nf, s);
     }

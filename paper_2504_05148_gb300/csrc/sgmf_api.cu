@@ -286,7 +286,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     // line kernels stay the default, the sweep is a tuning choice
     KParams kk = k;
     kk.num_paths = 8;
-    c->k.sweep_cs = kk.band == 0 ? agg_sweep_plan(kk, c->nb, &c->sweep_slots) : 0;
+    c->k.sweep_cs = agg_sweep_plan(kk, c->nb, &c->sweep_slots);
     c->sweep_ok = c->k.sweep_cs > 0;
     bool ok = !(c->sweep_ok && c->nb >= 2) ||
               (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
@@ -654,8 +654,8 @@ extern "C" sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t) {
     return fail(c, SGMF_ERR_ARG,
                 "sgmf_set_tuning: need line_warps in {1,2,4,8}, cost_px in {32,64,128} and sweep in {0,1}");
   if (t->sweep && !c->sweep_ok)
-    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: the sweep does not fit this context (banded, or a row wider "
-                                 "than one cluster holds)");
+    return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: the sweep does not fit this context (a row wider than one "
+                                 "cluster holds)");
   c->k.line_warps = t->line_warps;
   c->k.cost_px = t->cost_px;
   c->k.sweep = t->sweep;

@@ -43,6 +43,8 @@ struct SweepArgs {
   int *err;
   StepConsts sc;
   int strip;              // pixels per CTA (= 2 * warps * P)
+  const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]; null otherwise
+  int tw, th;
 };
 
 template <int CPL>
@@ -57,8 +59,10 @@ struct SweepCfg {
   // at least kExclusive bytes: one CTA per SM, so that the clusters the
   // device holds at once are the SMs the sweep occupies
   static constexpr int kExclusive = 120 * 1024;
+  // ring, barriers, exchange slots, one band-shift buffer (Dp u16) per group
   static constexpr int smem_bytes(int warps) {
-    return max(kExclusive, R * (2 * warps * P) * Dp + (R + 5) * 8 + 2 * 2 * (2 * warps) * kSlot * 4);
+    return max(kExclusive, R * (2 * warps * P) * Dp + (R + 5) * 8 + 2 * 2 * (2 * warps) * kSlot * 4 +
+                               (2 * warps) * Dp * 2);
   }
 };
 
@@ -110,7 +114,7 @@ __device__ __forceinline__ void sweep_step(uint32_t (&out)[NW], uint32_t &mout, 
   mout = group_min<NW>(out, grp);
 }
 
-template <int CPL>
+template <int CPL, bool BANDED>
 __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(const __grid_constant__ SweepArgs a) {
   using CF = SweepCfg<CPL>;
   constexpr int P = CF::P, NW = CF::NW, Dp = CF::Dp, R = CF::R, SL = CF::kSlot;
@@ -134,6 +138,15 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
   uint64_t *rowbar = bars + R;
   uint64_t *rx = bars + R + 1;
   uint32_t *slots = reinterpret_cast<uint32_t *>(bars + R + 5);   // [dir][parity][group][NW + 1][16]
+  uint16_t *shbuf = reinterpret_cast<uint16_t *>(slots + 2 * 2 * ng * SL) + gi * Dp;   // the group's shift scratch
+  // banded mode: a group's pixels share one band tile column (groups are 4
+  // pixels from a multiple of 4, tiles 8 wide)
+  constexpr bool banded = BANDED;
+  const int16_t *lo_f = banded ? a.lo + (size_t)f * a.th * a.tw : nullptr;
+  auto lo_at = [&](int x, int y) -> int {
+    x = min(max(x, 0), W - 1);
+    return lo_f[(y >> kBandTileLog) * a.tw + (x >> kBandTileLog)];
+  };
   const size_t fcells = frame_cells(a.k);
   const uint8_t *cost = a.cost + f * fcells;
   uint16_t *out = a.sum[up ? 1 : 0] + f * fcells + lig * CPL;
@@ -207,6 +220,24 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
   for (int t = 0; t < H; ++t) {
     bounded(&bars[t % R], (uint32_t)(t / R) & 1u);
     const uint8_t *st = ring + (size_t)(t % R) * strip * Dp + gi * P * Dp + lig * CPL;
+    const int y = up ? H - 1 - t : t, yp = up ? y + 1 : y - 1;   // this row, the previous one
+    int lo_cur = 0;
+    if constexpr (BANDED) {
+      // a new band tile row: every vector of the group moves to the new band
+      // (cells without a counterpart in the old band become absent)
+      lo_cur = lo_at(xg, y);
+      if (t > 0) {
+        const int delta = lo_cur - lo_at(xg, yp);
+        if (__any_sync(kFull, delta != 0)) {
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            band_shift<CPL>(V[i], delta, shbuf, lig);
+            band_shift<CPL>(DL[i], delta, shbuf, lig);
+            band_shift<CPL>(DR[i], delta, shbuf, lig);
+          }
+        }
+      }
+    }
     uint32_t C0[NW], CP[NW];
     unpack_u8<CPL>(st, z, C0);
     unpack_u8<CPL>(st + (P - 1) * Dp, z, CP);
@@ -246,6 +277,13 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
       }
       minL = sl[NW * 16];
       minR = sr[NW * 16];
+      if constexpr (BANDED) {
+        // the neighbours' vectors are in their own bands (pixel x - 1 or
+        // x + P of the previous row)
+        const int dl = lo_cur - lo_at(xg - 1, yp), dr = lo_cur - lo_at(xg + P, yp);
+        if (__any_sync(kFull, dl != 0)) band_shift<CPL>(inL, dl, shbuf, lig);
+        if (__any_sync(kFull, dr != 0)) band_shift<CPL>(inR, dr, shbuf, lig);
+      }
     }
     // the ring stage of row t - 2 is free: every warp finished that row before its row t - 1 arrival
     if (threadIdx.x == 0 && issued < H && issued <= t + 2) issue(issued);
@@ -333,7 +371,6 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
       }
       const int x = xg + i;
       if (ok && x < W) {
-        const int y = up ? H - 1 - t : t;
         uint32_t s[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) s[w] = V[i][w] + DL[i][w] + DR[i][w];
@@ -380,32 +417,32 @@ static cudaLaunchConfig_t sweep_config(int nf, int ctas, int warps, cudaStream_t
 
 // kernel attributes (once per device): the dynamic shared memory and cluster
 // sizes above the portable 8
-template <int CPL>
+template <int CPL, bool BANDED>
 static cudaError_t sweep_attributes() {
   static bool done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SweepCfg<CPL>::smem_bytes(SweepCfg<CPL>::kMaxWarps));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_agg_sweep<CPL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
 
 // The cluster size (CTAs per cluster) for the sweep of a context that runs
-// up to nb frames per call, or 0 when it cannot run (8 paths and the plain,
-// unbanded method only).  A call is 2 nb cluster jobs of H rows each; with n
+// up to nb frames per call, or 0 when it cannot run (8 paths only).  A call is 2 nb cluster jobs of H rows each; with n
 // clusters resident at once it takes ceil(2 nb / n) waves, and a row takes
 // time in proportion to the pixels of one CTA (one CTA per SM).  Among the
 // sizes from the smallest that holds a row up to twice that (at most 16) the
 // one with the fewest waves x pixels per CTA (ties: the smaller cluster).
-template <int CPL>
-int sweep_plan_t(const KParams &k, int nb, int *slots) {
+template <int CPL, bool BANDED>
+static int sweep_plan_b(const KParams &k, int nb, int *slots) {
   using CF = SweepCfg<CPL>;
-  if (k.num_paths != 8 || k.band != 0) return 0;
+  if (k.num_paths != 8) return 0;
   const int lo = (k.W + 2 * CF::kMaxWarps * CF::P - 1) / (2 * CF::kMaxWarps * CF::P);
-  if (lo > CF::kMaxCluster || sweep_attributes<CPL>() != cudaSuccess) {
+  if (lo > CF::kMaxCluster || sweep_attributes<CPL, BANDED>() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -417,7 +454,7 @@ int sweep_plan_t(const KParams &k, int nb, int *slots) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = sweep_config<CPL>(1, cs, warps, nullptr, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_agg_sweep<CPL>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_agg_sweep<CPL, BANDED>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -434,15 +471,23 @@ int sweep_plan_t(const KParams &k, int nb, int *slots) {
 }
 
 template <int CPL>
+int sweep_plan_t(const KParams &k, int nb, int *slots) {
+  return k.band ? sweep_plan_b<CPL, true>(k, nb, slots) : sweep_plan_b<CPL, false>(k, nb, slots);
+}
+
+template <int CPL>
 cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
   using CF = SweepCfg<CPL>;
   const int ctas = k.sweep_cs, warps = sweep_warps<CPL>(k.W, ctas);
   if (warps == 0) return cudaErrorInvalidValue;
-  cudaError_t e = sweep_attributes<CPL>();
+  cudaError_t e = k.band ? sweep_attributes<CPL, true>() : sweep_attributes<CPL, false>();
   if (e != cudaSuccess) return e;
   SweepArgs a;
-  a.k = k;
+  a.k = lane_params(k);                  // banded: lane cells are band positions
   a.cost = b.cost;
+  a.lo = k.band ? b.band_lo : nullptr;
+  a.tw = k.tw;
+  a.th = k.th;
   a.sum[0] = b.part[0];
   a.sum[1] = b.part[1];
   a.err = b.err;
@@ -451,7 +496,8 @@ cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStrea
   a.strip = 2 * warps * CF::P;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = sweep_config<CPL>(nf, ctas, warps, s, attr);
-  return cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL>, a);
+  return k.band ? cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL, true>, a)
+                : cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL, false>, a);
 }
 
 }  // namespace sgmf

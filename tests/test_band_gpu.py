@@ -16,11 +16,13 @@ def _tiles(W, H):
     return (H + S.BAND_TILE - 1) // S.BAND_TILE, (W + S.BAND_TILE - 1) // S.BAND_TILE
 
 
-def _gpu(scene, B, lo_tiles, params=None, lidar=True):
+def _gpu(scene, B, lo_tiles, params=None, lidar=True, sweep=0):
     import torch
     dev = torch.device("cuda:0")
     ctx = S.Context(scene.W, scene.H, scene.D, params, band=B)
     try:
+        if sweep:
+            S.sgmf_set_tuning(ctx.handle, 4, 128, 1)     # the cluster sweep on the bands
         ctx.set_debug(True)          # keeps the banded S of the frame for the comparison
         out = torch.empty(scene.shape, dtype=torch.int16, device=dev)
         ctx.compute_banded(torch.from_numpy(scene.left).to(dev), torch.from_numpy(scene.right).to(dev),
@@ -34,10 +36,10 @@ def _gpu(scene, B, lo_tiles, params=None, lidar=True):
         ctx.close()
 
 
-def _check(scene, B, lo_tiles, params=None, lidar=True):
+def _check(scene, B, lo_tiles, params=None, lidar=True, sweep=0):
     params = params or S.Params()
     lo_c = np.clip(lo_tiles, 0, scene.D - B).astype(np.int16)
-    g = _gpu(scene, B, lo_tiles, params, lidar)
+    g = _gpu(scene, B, lo_tiles, params, lidar, sweep)
     lo = oracle.expand_tiles(lo_c, scene.W, scene.H, S.BAND_TILE)
     o = oracle.compute_banded(scene.left, scene.right, scene.lidar if lidar else None, scene.D, B, lo,
                               oracle.Params(**vars(params)), volumes=True)
@@ -54,18 +56,21 @@ def _check(scene, B, lo_tiles, params=None, lidar=True):
     return g, o
 
 
+@pytest.mark.parametrize("sweep", [0, 1])
 @pytest.mark.parametrize("B", [64, 128])
-@pytest.mark.parametrize("W,H,D", [(256, 128, 128), (71, 29, 200), (130, 40, 256), (33, 17, 128), (200, 50, 160)])
-def test_random_band_tables(gpu, B, W, H, D):
+@pytest.mark.parametrize("W,H,D", [(256, 128, 128), (71, 29, 200), (130, 40, 256), (33, 17, 128), (200, 50, 160),
+                                   (1300, 20, 192)])
+def test_random_band_tables(gpu, B, W, H, D, sweep):
     if B > D:
         pytest.skip("band wider than the range")
     s = scenes.random_small(W * 3 + H + D + B, W, H, D)
     rng = np.random.default_rng(W + H + D + B)
     lo = rng.integers(-5, D - B + 6, size=_tiles(W, H))          # out-of-range starts get clamped
-    _check(s, B, lo)
+    _check(s, B, lo, sweep=sweep)
 
 
-def test_smooth_bands_from_the_truth(gpu):
+@pytest.mark.parametrize("sweep", [0, 1])
+def test_smooth_bands_from_the_truth(gpu, sweep):
     s = scenes.kitti(2700)
     B = 64
     th, tw = _tiles(s.W, s.H)
@@ -75,7 +80,7 @@ def test_smooth_bands_from_the_truth(gpu):
         for tx in range(tw):
             blk = s.truth[T * ty:T * ty + T, T * tx:T * tx + T]
             lo[ty, tx] = int(np.median(blk)) - B // 2
-    g, o = _check(s, B, lo)
+    g, o = _check(s, B, lo, sweep=sweep)
     assert (g["out"] >= 0).mean() > 0.5
 
 
@@ -87,17 +92,19 @@ def test_full_range_band_is_the_plain_method(gpu):
     np.testing.assert_array_equal(g["out"], want)
 
 
+@pytest.mark.parametrize("sweep", [0, 1])
 @pytest.mark.parametrize("case", ["dsgm", "four_paths", "u16_spill", "no_lidar", "census_full"])
-def test_parameter_variants(gpu, case):
+def test_parameter_variants(gpu, case, sweep):
     s = scenes.random_small(9200, 97, 45, 192)
     rng = np.random.default_rng(9)
     lo = rng.integers(0, 192 - 64 + 1, size=_tiles(97, 45))
     p = {"dsgm": S.Params(semidense=0), "four_paths": S.Params(num_paths=4), "u16_spill": S.Params(p2=300),
          "no_lidar": S.Params(), "census_full": S.Params(census=S.SGMF_CENSUS_9X7)}[case]
-    _check(s, 64, lo, p, lidar=case != "no_lidar")
+    _check(s, 64, lo, p, lidar=case != "no_lidar", sweep=sweep)
 
 
-def test_batch(gpu):
+@pytest.mark.parametrize("sweep", [0, 1])
+def test_batch(gpu, sweep):
     import torch
     dev = torch.device("cuda:0")
     scs = [scenes.random_small(9300 + i, 120, 50, 128) for i in range(3)]
@@ -105,6 +112,8 @@ def test_batch(gpu):
     los = [rng.integers(0, 65, size=_tiles(120, 50)).astype(np.int16) for _ in scs]
     ctx = S.Context(120, 50, 128, band=64, max_batch=3)
     try:
+        if sweep:
+            S.sgmf_set_tuning(ctx.handle, 4, 128, 1)
         out = torch.empty((3, 50, 120), dtype=torch.int16, device=dev)
         ctx.compute_banded(torch.from_numpy(np.stack([s.left for s in scs])).to(dev),
                            torch.from_numpy(np.stack([s.right for s in scs])).to(dev),

@@ -4,7 +4,8 @@ row by row, exchanging edge vectors between groups and CTAs.  Its S, d*, d'
 and output must equal the oracle's bit for bit on clusters of one to eight
 CTAs with ragged last strips and groups, every lane width, the u16 path-cost
 range, sub-pixel output and batches; where it does not fit, the context keeps
-the line kernels and refuses the tuning."""
+the line kernels and refuses the tuning.  (Its banded mode is tested with the
+other banded cases.)"""
 import numpy as np
 import pytest
 
@@ -110,7 +111,7 @@ def test_four_paths_keep_the_line_kernel(gpu):
 
 
 def test_sweep_refused_where_it_does_not_fit(gpu):
-    # a row wider than sixteen CTAs of 160 pixels (Dp = 128), and a banded context
+    # a row wider than sixteen CTAs of 160 pixels (Dp = 128)
     ctx = S.Context(2600, 8, 128)
     try:
         assert S.sgmf_get_tuning(ctx.handle)[2] == 0
@@ -119,11 +120,12 @@ def test_sweep_refused_where_it_does_not_fit(gpu):
         assert e.value.status == S.SGMF_ERR_ARG
     finally:
         ctx.close()
+    # a banded context takes the sweep (off by default)
     h = S.sgmf_create_banded(256, 32, 128, 64, 1)
     try:
         assert S.sgmf_get_tuning(h)[2] == 0
-        with pytest.raises(S.SgmfError):
-            S.sgmf_set_tuning(h, 4, 128, 1)
+        S.sgmf_set_tuning(h, 4, 128, 1)
+        assert S.sgmf_get_tuning(h)[2] == 1
     finally:
         S.sgmf_destroy(h)
 
@@ -152,4 +154,34 @@ def test_split_batch_matches_oracle(gpu):
         ctx.close()
     for i, s in enumerate(scs):
         np.testing.assert_array_equal(got[i], oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out,
+                                      err_msg=f"frame {i}")
+
+
+def test_bench_configuration_at_full_size(gpu):
+    """The timed configuration: 32 KITTI-shaped frames in one call through the
+    sweep (in parts of one sweep wave, row kernels on the second stream).
+    Every frame equals the line-kernel path's; the first frame, the first of
+    the second part and the last also equal the oracle."""
+    import torch
+    dev = torch.device("cuda:0")
+    n = 32
+    scs = [scenes.kitti(12000 + i) for i in range(n)]
+    l = torch.from_numpy(np.stack([s.left for s in scs])).to(dev)
+    r = torch.from_numpy(np.stack([s.right for s in scs])).to(dev)
+    li = torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev)
+    got = {}
+    for sweep in (1, 0):
+        ctx = S.Context(1242, 375, 128, max_batch=n)
+        try:
+            S.sgmf_set_tuning(ctx.handle, 4, 128, sweep)
+            out = torch.empty((n, 375, 1242), dtype=torch.int16, device=dev)
+            ctx.compute(l, r, li, out)
+            ctx.sync()
+            got[sweep] = out.cpu().numpy()
+        finally:
+            ctx.close()
+    np.testing.assert_array_equal(got[1], got[0])
+    for i in (0, 13, n - 1):
+        s = scs[i]
+        np.testing.assert_array_equal(got[1][i], oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out,
                                       err_msg=f"frame {i}")
