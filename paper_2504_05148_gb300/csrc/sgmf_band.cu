@@ -23,14 +23,21 @@ cudaError_t launch_band_clamp(const KParams &k, const Buffers &b, int nf, const 
 }
 
 // Banded cost: cell j of pixel p holds C-bar(p, lo_p + j) (Eq. 4, the plain
-// rules).  A CTA handles 64 pixels (several tiles) of one row; the right-census
-// window covering all their bands is staged in shared memory and the lanes
-// of a warp walk the cells of one pixel.
-constexpr int kBandCostPx = 64;
+// rules).  A CTA handles 128 pixels (several tiles) of one row; the right-census
+// window covering all their bands is staged in shared memory, VL times with
+// shifts as in the plain cost kernel, and a lane of a warp owns B / 32
+// consecutive cells of one pixel, read as one aligned vector and stored as
+// packed bytes.  Pixels with a prior take the far class in the loop; one
+// thread per pixel rewrites the (at most three) cells with |d - prior| <= 1.
+constexpr int kBandCostPx = 128;
 
 template <typename CT, int B>
 __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
-  __shared__ CT cr_s[kBandCostPx + B + kMaxDisp];
+  constexpr int DPL = B / 32;
+  using CV = CostVec<CT, DPL>;
+  constexpr int VL = CV::VL, NV = DPL / VL;
+  constexpr int NWIN = kBandCostPx + kMaxDisp;    // >= the window span, kBandCostPx - 1 + D
+  __shared__ __align__(16) CT cr_s[VL][NWIN];    // copy k: cr_s[k][i] = cR(base + i + k)
   __shared__ CT cl_s[kBandCostPx];
   __shared__ int pd_s[kBandCostPx];
   __shared__ int lo_s[kBandCostPx / kBandTile];
@@ -54,13 +61,15 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
     lo_min = min(lo_min, lo_s[t]);
     lo_max = max(lo_max, lo_s[t]);
   }
-  // cr_s[i] = cR(base + i) covers x - d for every pixel x and d in its band
+  // cR(x - (lo + j)) is entry px + (lo_max - lo) + B - 1 - j of the window
   const int base = x0 - lo_max - (B - 1);
-  const int span = (npx - 1) + (lo_max - lo_min) + B;   // <= 63 + (D - B) + B
-  for (int i = threadIdx.x; i < span; i += blockDim.x) {
-    const int xx = base + i;
-    cr_s[i] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
-  }
+  const int span = (npx - 1) + (lo_max - lo_min) + B;   // <= kBandCostPx - 1 + D
+#pragma unroll
+  for (int kk = 0; kk < VL; ++kk)
+    for (int j = threadIdx.x; j < span - kk; j += blockDim.x) {
+      const int xx = base + j + kk;
+      cr_s[kk][j] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
+    }
   if (threadIdx.x < kBandCostPx) {
     const int xx = x0 + threadIdx.x;
     cl_s[threadIdx.x] = xx < W ? cl[xx] : (CT)0;
@@ -68,6 +77,7 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = DPL * lane;                      // the lane's first cell
   // every pixel of the CTA has x - d >= 0 for all its band cells
   const bool inner = x0 >= lo_max + B - 1;
   for (int px = warp; px < npx; px += 8) {
@@ -75,36 +85,52 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
     const CT c = cl_s[px];
     const int pd = pd_s[px];
     const int lo = lo_s[px >> kBandTileLog];
-    if (inner && pd < 0) {   // warp-uniform: without a prior C-bar = H
+    // the lane's run: entries of cells c0 + DPL - 1 .. c0, on a vector boundary of copy kk
+    const int off = px + lo_max - lo;
+    const int kk = off % VL;
+    const CT *run = &cr_s[kk][off + B - DPL * (lane + 1) - kk];
+    CT v[DPL];
 #pragma unroll
-      for (int m = 0; m < B / 32; ++m) {
-        const int j = lane + 32 * m;
-        const CT r = cr_s[x - (lo + j) - base];
-        if constexpr (sizeof(CT) == 4)
-          out_s[px * B + j] = (uint8_t)__popc(c ^ r);
-        else
-          out_s[px * B + j] = (uint8_t)__popcll(c ^ r);
-      }
-      continue;
+    for (int q = 0; q < NV; ++q) {
+      const typename CV::V t = reinterpret_cast<const typename CV::V *>(run)[q];
+      const CT *e = reinterpret_cast<const CT *>(&t);
+#pragma unroll
+      for (int m = 0; m < VL; ++m) v[q * VL + m] = e[m];
     }
+    uint32_t out[DPL];
+    if (inner) {
 #pragma unroll
-    for (int m = 0; m < B / 32; ++m) {
-      const int j = lane + 32 * m, d = lo + j;
-      int h;
-      if (x >= d) {
-        const CT r = cr_s[x - d - base];
-        if constexpr (sizeof(CT) == 4)
-          h = __popc(c ^ r);
-        else
-          h = __popcll(c ^ r);
-      } else {
-        h = k.nbits;
+      for (int i = 0; i < DPL; ++i) out[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
+      if (pd >= 0) {
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) out[i] = tab_s[2 * 64 + out[i]];   // far class; near cells below
       }
-      const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
-      out_s[px * B + j] = tab_s[cls * 64 + h];
+    } else {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        const int d = lo + c0 + i;
+        const int h = x >= d ? hamming<CT>(c, v[DPL - 1 - i]) : k.nbits;
+        const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
+        out[i] = tab_s[cls * 64 + h];
+      }
+    }
+    store_cost_bytes<DPL>(out_s + px * B + c0, out);
+  }
+  __syncthreads();
+  if (inner && threadIdx.x < npx) {
+    const int px = threadIdx.x, pd = pd_s[px], lo = lo_s[px >> kBandTileLog];
+    if (pd >= 0) {
+      const CT c = cl_s[px];
+#pragma unroll
+      for (int j = -1; j <= 1; ++j) {
+        const int cell = pd + j - lo;
+        if (cell >= 0 && cell < B)
+          out_s[px * B + cell] = tab_s[abs(j) * 64 + hamming<CT>(c, cr_s[0][px + lo_max - lo + B - 1 - cell])];
+      }
     }
   }
   __syncthreads();
+  // the block's [npx][B] bytes are contiguous in the banded cost volume
   uint4 *dst = reinterpret_cast<uint4 *>(b.cost + (rowp + x0) * B);
   const uint4 *src = reinterpret_cast<const uint4 *>(out_s);
   for (int i = threadIdx.x; i < npx * B / 16; i += blockDim.x) dst[i] = src[i];

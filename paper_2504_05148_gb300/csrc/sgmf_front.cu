@@ -7,8 +7,6 @@
 #include <cuda.h>
 #include <cstdint>
 
-#include <type_traits>
-
 #include "sgmf_internal.cuh"
 
 namespace sgmf {
@@ -409,47 +407,13 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 // in shared memory, leave as 16-byte stores (cells d >= D hold 0).
 
 
-template <typename CT>
-__device__ __forceinline__ int hamming(CT a, CT b) {
-  if constexpr (sizeof(CT) == 4)
-    return __popc(a ^ b);
-  else
-    return __popcll(a ^ b);
-}
 
 // A lane owns DPL consecutive disparities d0 = DPL * lane .. d0 + DPL - 1 of
 // a pixel, whose right-census words cR(x - d) are DPL consecutive entries of
-// the staged window.  They are read as aligned vectors: the window is staged
-// VL times, copy k shifted by k entries, and a pixel reads the copy that
-// puts its run on a vector boundary (lanes DPL entries apart: one vector
+// the staged window.  They are read as aligned vectors (CostVec): the window
+// is staged VL times, copy k shifted by k entries, and a pixel reads the copy
+// that puts its run on a vector boundary (lanes DPL entries apart: one vector
 // per lane, no bank conflicts).  The lane packs its cost bytes into words.
-template <typename CT, int DPL>
-struct CostVec {
-  // entries per vector load: 16 bytes, or 8 when DPL is not a multiple of 4 words
-  static constexpr int VL = sizeof(CT) == 8 ? 2 : (DPL % 4 == 0 ? 4 : 2);
-  using V = typename std::conditional<VL * sizeof(CT) == 16, uint4, uint2>::type;
-};
-
-template <int DPL>
-__device__ __forceinline__ void store_cost_bytes(uint8_t *o, const uint32_t (&b)[DPL]) {
-  uint32_t w[(DPL + 3) / 4];
-#pragma unroll
-  for (int j = 0; j < DPL / 4; ++j)
-    w[j] = prmt(prmt(b[4 * j], b[4 * j + 1], 0x1140), prmt(b[4 * j + 2], b[4 * j + 3], 0x1140), 0x5410);
-  if constexpr (DPL == 2) {
-    *reinterpret_cast<uint16_t *>(o) = (uint16_t)prmt(b[0], b[1], 0x1140);
-  } else if constexpr (DPL == 4) {
-    *reinterpret_cast<uint32_t *>(o) = w[0];
-  } else if constexpr (DPL == 6) {   // 2-byte aligned
-    uint16_t *q = reinterpret_cast<uint16_t *>(o);
-    q[0] = (uint16_t)prmt(b[0], b[1], 0x1140);
-    q[1] = (uint16_t)prmt(b[2], b[3], 0x1140);
-    q[2] = (uint16_t)prmt(b[4], b[5], 0x1140);
-  } else {
-    *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
-  }
-}
-
 template <typename CT, int DPL, int PX>
 __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
   constexpr int Dp = 32 * DPL;

@@ -15,6 +15,7 @@
 
 #include <cstdint>
 #include <string>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "sgmf.h"
@@ -94,6 +95,43 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
   return __byte_perm(a, b, s);
 }
+
+// ---- cost kernels: vector reads of the right census, packed cost bytes ------
+template <typename CT>
+__device__ __forceinline__ int hamming(CT a, CT b) {
+  if constexpr (sizeof(CT) == 4)
+    return __popc(a ^ b);
+  else
+    return __popcll(a ^ b);
+}
+
+template <typename CT, int DPL>
+struct CostVec {
+  // entries per vector load: 16 bytes, or 8 when DPL is not a multiple of 4 words
+  static constexpr int VL = sizeof(CT) == 8 ? 2 : (DPL % 4 == 0 ? 4 : 2);
+  using V = typename std::conditional<VL * sizeof(CT) == 16, uint4, uint2>::type;
+};
+
+template <int DPL>
+__device__ __forceinline__ void store_cost_bytes(uint8_t *o, const uint32_t (&b)[DPL]) {
+  uint32_t w[(DPL + 3) / 4];
+#pragma unroll
+  for (int j = 0; j < DPL / 4; ++j)
+    w[j] = prmt(prmt(b[4 * j], b[4 * j + 1], 0x1140), prmt(b[4 * j + 2], b[4 * j + 3], 0x1140), 0x5410);
+  if constexpr (DPL == 2) {
+    *reinterpret_cast<uint16_t *>(o) = (uint16_t)prmt(b[0], b[1], 0x1140);
+  } else if constexpr (DPL == 4) {
+    *reinterpret_cast<uint32_t *>(o) = w[0];
+  } else if constexpr (DPL == 6) {   // 2-byte aligned
+    uint16_t *q = reinterpret_cast<uint16_t *>(o);
+    q[0] = (uint16_t)prmt(b[0], b[1], 0x1140);
+    q[1] = (uint16_t)prmt(b[2], b[3], 0x1140);
+    q[2] = (uint16_t)prmt(b[4], b[5], 0x1140);
+  } else {
+    *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+  }
+}
+
 
 // sticky error word: first error wins
 __device__ __forceinline__ void set_error(int *err, int code) {
