@@ -632,6 +632,23 @@ def main():
     ctx.sync()
     launches = args.steps * ctx.launches_per_compute()
 
+    # With the sweep, a batch runs in parts whose row kernels share the GPU
+    # with the next part's sweep, which lengthens the sweep's own event-timed
+    # duration.  The same kernels on the same frames once more in one launch
+    # each (parts off), a few steps after the timed region, give the
+    # dominant kernel's duration when it has the GPU to itself.
+    iso_times: dict[str, list[float]] = {}
+    cur = sgmf.sgmf_tuning_of(ctx.handle)
+    if cur.sweep and cur.parts:
+        sgmf.sgmf_set_tuning(ctx.handle, cur.line_warps, cur.cost_px, cur.sweep, 0)
+        for i in range(5):
+            a, b = step()
+            b.synchronize()
+            if i >= 2:
+                for name, ms in ctx.kernel_times():
+                    iso_times.setdefault(name, []).append(ms)
+        sgmf.sgmf_set_tuning(ctx.handle, cur.line_warps, cur.cost_px, cur.sweep, 1)
+
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if pg:
         import torch.distributed as dist
@@ -768,6 +785,12 @@ def main():
         roof["kernel_ms_avg"] = avg[dom]
         roof["hbm_frac_algorithmic"] = alg["bytes"] / t_s / 1e9 / peaks["hbm_gbs"]
         roof["alu_frac_algorithmic"] = alg["ops"] / t_s / alu_peak
+        if iso_times.get(dom):
+            t_iso = sum(iso_times[dom]) / len(iso_times[dom]) * 1e-3
+            roof["alone"] = {"kernel_ms_avg": t_iso * 1e3, "achieved": alg["ops"] / t_iso / 1e12,
+                             "frac": alg["ops"] / t_iso / alu_peak,
+                             "note": "the same launches with parts off (the GPU to itself), 3 steps after the "
+                                     "timed region; frac above is inside the timed pipeline"}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world > 1 and False):

@@ -339,6 +339,10 @@ typedef struct {
                              picks the cluster size that keeps the most CTAs
                              resident), and is refused otherwise; it takes effect
                              with 8 paths. */
+    int32_t parts;        /* with the sweep: 1 (default) runs a batch in parts of one
+                             sweep wave, each part's row kernel on a second stream
+                             beside the next part's sweep; 0 runs the whole batch
+                             through each kernel in one launch.  0 or 1. */
 } sgmf_tuning;
 
 /* Set / read the context's tuning.  SGMF_ERR_ARG for other values. */

@@ -236,6 +236,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   k.line_warps = 4;
   k.cost_px = 128;
   k.sweep = 0;
+  k.parts = 1;
   sgmf_params def;
   sgmf_default_params(&def);
   apply_params(c, def);
@@ -366,7 +367,7 @@ static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths =
 // cluster jobs, the resident count or its smallest even multiple), so the
 // parts add no wave; at most kMaxParts parts.
 static int sweep_part(const sgmf_ctx *c, int n) {
-  if (!c->side || c->sweep_slots < 1 || n < 2) return 0;
+  if (!c->k.parts || !c->side || c->sweep_slots < 1 || n < 2) return 0;
   int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 m % slots == 0
   if (m >= n) return 0;
   while ((n + m - 1) / m > sgmf_ctx::kMaxParts) m *= 2;
@@ -645,20 +646,22 @@ extern "C" size_t sgmf_device_bytes(const sgmf_ctx *c) { return c ? c->bytes : 0
 // ---- launch tuning -------------------------------------------------------------
 static bool valid_tuning(const sgmf_tuning &t) {
   return (t.line_warps == 1 || t.line_warps == 2 || t.line_warps == 4 || t.line_warps == 8) &&
-         (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128) && (t.sweep == 0 || t.sweep == 1);
+         (t.cost_px == 32 || t.cost_px == 64 || t.cost_px == 128) && (t.sweep == 0 || t.sweep == 1) &&
+         (t.parts == 0 || t.parts == 1);
 }
 
 extern "C" sgmf_status sgmf_set_tuning(sgmf_ctx *c, const sgmf_tuning *t) {
   if (!c || !t) return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: NULL argument");
   if (!valid_tuning(*t))
     return fail(c, SGMF_ERR_ARG,
-                "sgmf_set_tuning: need line_warps in {1,2,4,8}, cost_px in {32,64,128} and sweep in {0,1}");
+                "sgmf_set_tuning: need line_warps in {1,2,4,8}, cost_px in {32,64,128}, sweep and parts in {0,1}");
   if (t->sweep && !c->sweep_ok)
     return fail(c, SGMF_ERR_ARG, "sgmf_set_tuning: the sweep does not fit this context (a row wider than one "
                                  "cluster holds)");
   c->k.line_warps = t->line_warps;
   c->k.cost_px = t->cost_px;
   c->k.sweep = t->sweep;
+  c->k.parts = t->parts;
   return SGMF_OK;
 }
 
@@ -667,6 +670,7 @@ extern "C" sgmf_status sgmf_get_tuning(const sgmf_ctx *c, sgmf_tuning *t) {
   t->line_warps = c->k.line_warps;
   t->cost_px = c->k.cost_px;
   t->sweep = c->k.sweep;
+  t->parts = c->k.parts;
   return SGMF_OK;
 }
 
@@ -679,7 +683,7 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
   c->profiling = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   sgmf_status st = SGMF_OK;
-  sgmf_tuning keep{c->k.line_warps, c->k.cost_px, c->k.sweep}, win = keep;
+  sgmf_tuning keep{c->k.line_warps, c->k.cost_px, c->k.sweep, c->k.parts}, win = keep;
   float win_ms = 0.0f;
   bool have = false;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -719,7 +723,7 @@ extern "C" sgmf_status sgmf_autotune(sgmf_ctx *c, int n, const uint8_t *left, co
     if (!have || med < win_ms) {
       have = true;
       win_ms = med;
-      win = sgmf_tuning{c->k.line_warps, c->k.cost_px, c->k.sweep};
+      win = sgmf_tuning{c->k.line_warps, c->k.cost_px, c->k.sweep, c->k.parts};
     }
   }
   if (e0) cudaEventDestroy(e0);

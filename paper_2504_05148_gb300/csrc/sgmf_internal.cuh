@@ -42,6 +42,7 @@ struct KParams {
   int line_warps, cost_px;    // tuning: warps per line-kernel CTA, pixels per cost-kernel CTA
   int sweep;                  // tuning: 1 = row-synchronous sweep instead of the line kernels
   int sweep_cs;               // CTAs per sweep cluster (0: the sweep cannot run this context)
+  int parts;                  // tuning: 1 = sweep batches in parts (row kernels on a second stream)
   int band;                   // banded mode: band width B (= Dp); 0 = the plain method
   int tw, th;                 // banded mode: band tiles per row / column                  // census bits (31 or 62)
 };

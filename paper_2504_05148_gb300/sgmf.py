@@ -58,7 +58,8 @@ class sgmf_params(ctypes.Structure):
 
 
 class sgmf_tuning(ctypes.Structure):
-    _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32), ("sweep", ctypes.c_int32)]
+    _fields_ = [("line_warps", ctypes.c_int32), ("cost_px", ctypes.c_int32), ("sweep", ctypes.c_int32),
+                ("parts", ctypes.c_int32)]
 
 
 class sgmf_server_counters(ctypes.Structure):
@@ -386,9 +387,16 @@ def sgmf_bn_tiles(n: int, width: int, height: int, max_disp: int, band: int, con
                                stream or None), None)
 
 
-def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int, sweep: int = 0) -> None:
-    t = sgmf_tuning(line_warps, cost_px, sweep)
+def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int, sweep: int = 0, parts: int = 1) -> None:
+    t = sgmf_tuning(line_warps, cost_px, sweep, parts)
     _check(lib().sgmf_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def sgmf_tuning_of(ctx: int) -> sgmf_tuning:
+    """The context's whole tuning struct (sgmf_get_tuning returns its first three fields)."""
+    t = sgmf_tuning()
+    _check(lib().sgmf_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t
 
 
 def sgmf_get_tuning(ctx: int) -> tuple[int, int, int]:

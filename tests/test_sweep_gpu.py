@@ -142,6 +142,7 @@ def test_split_batch_matches_oracle(gpu):
     ctx = S.Context(W, H, D, max_batch=n)
     try:
         S.sgmf_set_tuning(ctx.handle, 4, 128, 1)
+        assert S.sgmf_tuning_of(ctx.handle).parts == 1
         out = torch.empty((n, H, W), dtype=torch.int16, device=dev)
         for _ in range(2):                 # twice: the events and the second stream are reused
             out.fill_(-7)
@@ -150,6 +151,16 @@ def test_split_batch_matches_oracle(gpu):
                         torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev), out)
             ctx.sync()
         got = out.cpu().numpy()
+        # the whole batch in one launch per kernel gives the same output
+        S.sgmf_set_tuning(ctx.handle, 4, 128, 1, 0)
+        out.fill_(-7)
+        ctx.compute(torch.from_numpy(np.stack([s.left for s in scs])).to(dev),
+                    torch.from_numpy(np.stack([s.right for s in scs])).to(dev),
+                    torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev), out)
+        ctx.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), got)
+        with pytest.raises(S.SgmfError):
+            S.sgmf_set_tuning(ctx.handle, 4, 128, 1, 2)
     finally:
         ctx.close()
     for i, s in enumerate(scs):
