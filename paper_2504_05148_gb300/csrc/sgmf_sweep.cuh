@@ -47,12 +47,15 @@ struct SweepArgs {
   int tw, th;
 };
 
-template <int CPL>
+template <int CPL, bool BANDED>
 struct SweepCfg {
   static constexpr int Dp = 16 * CPL, NW = CPL / 2;
-  static constexpr int P = 4;                    // pixels per group
-  // warps per CTA: 20 (96 registers a thread) up to 8 cells per lane, 10 above
-  static constexpr int kMaxWarps = CPL <= 8 ? 20 : 10;
+  // pixels per group and warps per CTA: 8 pixels and 10 warps (168
+  // registers a thread) up to 8 cells per lane; 4 pixels and 20 warps (96
+  // registers) for the banded variant there, whose band bookkeeping would
+  // spill at 8; 4 pixels and 10 warps above 8 cells per lane
+  static constexpr int P = CPL <= 8 && !BANDED ? 8 : 4;
+  static constexpr int kMaxWarps = CPL <= 8 && BANDED ? 20 : 10;
   static constexpr int kMaxCluster = 16;         // CTAs per cluster (above 8: non-portable)
   static constexpr int R = 4;                    // ring stages (rows)
   static constexpr int kSlot = (NW + 1) * 16;    // words of one exchanged vector: NW words + m, per lane
@@ -115,8 +118,9 @@ __device__ __forceinline__ void sweep_step(uint32_t (&out)[NW], uint32_t &mout, 
 }
 
 template <int CPL, bool BANDED>
-__global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(const __grid_constant__ SweepArgs a) {
-  using CF = SweepCfg<CPL>;
+__global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
+    k_agg_sweep(const __grid_constant__ SweepArgs a) {
+  using CF = SweepCfg<CPL, BANDED>;
   constexpr int P = CF::P, NW = CF::NW, Dp = CF::Dp, R = CF::R, SL = CF::kSlot;
   constexpr uint32_t kMsgBytes = SL * 4;            // one exchanged vector: 16 lanes x (NW + 1) words
   extern __shared__ __align__(128) uint8_t smem[];
@@ -390,21 +394,21 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL>::kMaxWarps, 1) k_agg_sweep(
 
 // Warps per CTA when a row of W pixels is split over `ctas` CTAs, or 0 when
 // that split is not allowed (a CTA above kMaxWarps, or an empty last CTA).
-template <int CPL>
+template <int CPL, bool BANDED>
 inline int sweep_warps(int W, int ctas) {
-  using CF = SweepCfg<CPL>;
+  using CF = SweepCfg<CPL, BANDED>;
   if (ctas < 1 || ctas > CF::kMaxCluster) return 0;
   const int warps = (W + ctas * 2 * CF::P - 1) / (ctas * 2 * CF::P);
   if (warps > CF::kMaxWarps || (ctas - 1) * 2 * warps * CF::P >= W) return 0;
   return warps;
 }
 
-template <int CPL>
+template <int CPL, bool BANDED>
 static cudaLaunchConfig_t sweep_config(int nf, int ctas, int warps, cudaStream_t s, cudaLaunchAttribute *attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctas, 2, nf);
   cfg.blockDim = dim3(32 * warps);
-  cfg.dynamicSmemBytes = SweepCfg<CPL>::smem_bytes(warps);
+  cfg.dynamicSmemBytes = SweepCfg<CPL, BANDED>::smem_bytes(warps);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = ctas;
@@ -424,7 +428,7 @@ static cudaError_t sweep_attributes() {
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SweepCfg<CPL>::smem_bytes(SweepCfg<CPL>::kMaxWarps));
+                                       SweepCfg<CPL, BANDED>::smem_bytes(SweepCfg<CPL, BANDED>::kMaxWarps));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
@@ -439,7 +443,7 @@ static cudaError_t sweep_attributes() {
 // one with the fewest waves x pixels per CTA (ties: the smaller cluster).
 template <int CPL, bool BANDED>
 static int sweep_plan_b(const KParams &k, int nb, int *slots) {
-  using CF = SweepCfg<CPL>;
+  using CF = SweepCfg<CPL, BANDED>;
   if (k.num_paths != 8) return 0;
   const int lo = (k.W + 2 * CF::kMaxWarps * CF::P - 1) / (2 * CF::kMaxWarps * CF::P);
   if (lo > CF::kMaxCluster || sweep_attributes<CPL, BANDED>() != cudaSuccess) {
@@ -449,10 +453,10 @@ static int sweep_plan_b(const KParams &k, int nb, int *slots) {
   int best = 0, best_n = 0;
   long best_cost = 0;
   for (int cs = lo; cs <= min(CF::kMaxCluster, 2 * lo); ++cs) {
-    const int warps = sweep_warps<CPL>(k.W, cs);
+    const int warps = sweep_warps<CPL, BANDED>(k.W, cs);
     if (warps == 0) continue;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = sweep_config<CPL>(1, cs, warps, nullptr, attr);
+    cudaLaunchConfig_t cfg = sweep_config<CPL, BANDED>(1, cs, warps, nullptr, attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, k_agg_sweep<CPL, BANDED>, &cfg) != cudaSuccess) {
       cudaGetLastError();
@@ -475,17 +479,17 @@ int sweep_plan_t(const KParams &k, int nb, int *slots) {
   return k.band ? sweep_plan_b<CPL, true>(k, nb, slots) : sweep_plan_b<CPL, false>(k, nb, slots);
 }
 
-template <int CPL>
-cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
-  using CF = SweepCfg<CPL>;
-  const int ctas = k.sweep_cs, warps = sweep_warps<CPL>(k.W, ctas);
+template <int CPL, bool BANDED>
+static cudaError_t launch_sweep_b(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  using CF = SweepCfg<CPL, BANDED>;
+  const int ctas = k.sweep_cs, warps = sweep_warps<CPL, BANDED>(k.W, ctas);
   if (warps == 0) return cudaErrorInvalidValue;
-  cudaError_t e = k.band ? sweep_attributes<CPL, true>() : sweep_attributes<CPL, false>();
+  cudaError_t e = sweep_attributes<CPL, BANDED>();
   if (e != cudaSuccess) return e;
   SweepArgs a;
   a.k = lane_params(k);                  // banded: lane cells are band positions
   a.cost = b.cost;
-  a.lo = k.band ? b.band_lo : nullptr;
+  a.lo = BANDED ? b.band_lo : nullptr;
   a.tw = k.tw;
   a.th = k.th;
   a.sum[0] = b.part[0];
@@ -495,9 +499,13 @@ cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStrea
   a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
   a.strip = 2 * warps * CF::P;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = sweep_config<CPL>(nf, ctas, warps, s, attr);
-  return k.band ? cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL, true>, a)
-                : cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL, false>, a);
+  cudaLaunchConfig_t cfg = sweep_config<CPL, BANDED>(nf, ctas, warps, s, attr);
+  return cudaLaunchKernelEx(&cfg, k_agg_sweep<CPL, BANDED>, a);
+}
+
+template <int CPL>
+cudaError_t launch_sweep_t(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
+  return k.band ? launch_sweep_b<CPL, true>(k, b, nf, s) : launch_sweep_b<CPL, false>(k, b, nf, s);
 }
 
 }  // namespace sgmf

@@ -111,8 +111,8 @@ def test_four_paths_keep_the_line_kernel(gpu):
 
 
 def test_sweep_refused_where_it_does_not_fit(gpu):
-    # a row wider than sixteen CTAs of 160 pixels (Dp = 128)
-    ctx = S.Context(2600, 8, 128)
+    # a row wider than sixteen CTAs of 192 pixels (Dp = 128)
+    ctx = S.Context(3200, 8, 128)
     try:
         assert S.sgmf_get_tuning(ctx.handle)[2] == 0
         with pytest.raises(S.SgmfError) as e:
