@@ -333,8 +333,8 @@ typedef struct {
                              row-synchronous sweeps of a thread-block cluster per
                              frame (one launch) instead of the three line kernels
                              (line_warps is then unused).  0 (default) or 1; 1 needs
-                             the plain (unbanded) method, a row of at most 16 CTAs x
-                             160 pixels (Dp <= 128) or 16 x 80 pixels (Dp > 128) and
+                             a row of at most 16 CTAs x 128 pixels (Dp <= 128; banded:
+                             x 160) or 16 x 80 pixels (Dp > 128) and
                              a device that can place such a cluster (the context
                              picks the cluster size that keeps the most CTAs
                              resident), and is refused otherwise; it takes effect

@@ -48,11 +48,11 @@ def _check(scene, params=None):
     return g
 
 
-# (W, H, D): clusters of 8 to 16 CTAs with a ragged last strip (1242, 2400),
+# (W, H, D): clusters of 8 to 16 CTAs with a ragged last strip (1242, 2040),
 # full CTAs (1280 at Dp = 64), the two wide lane widths at their widest rows
 # (1280 at Dp = 256), ragged groups inside one CTA, one-pixel-wide and
 # one-row frames
-SHAPES = [(1242, 24, 128), (2400, 6, 128), (1280, 12, 64), (1280, 6, 256), (640, 14, 256), (300, 30, 192),
+SHAPES = [(1242, 24, 128), (2040, 6, 128), (1280, 12, 64), (1280, 6, 256), (640, 14, 256), (300, 30, 192),
           (161, 21, 128), (17, 9, 100), (1, 5, 16), (2, 3, 3), (9, 1, 64), (33, 40, 64)]
 
 
@@ -111,7 +111,7 @@ def test_four_paths_keep_the_line_kernel(gpu):
 
 
 def test_sweep_refused_where_it_does_not_fit(gpu):
-    # a row wider than sixteen CTAs of 192 pixels (Dp = 128)
+    # a row wider than sixteen CTAs of 128 pixels (Dp = 128)
     ctx = S.Context(3200, 8, 128)
     try:
         assert S.sgmf_get_tuning(ctx.handle)[2] == 0
