@@ -50,10 +50,10 @@ struct SweepArgs {
 template <int CPL, bool BANDED>
 struct SweepCfg {
   static constexpr int Dp = 16 * CPL, NW = CPL / 2;
-  // pixels per group and warps per CTA: 8 pixels and 8 warps (168 registers
-  // a thread) up to 8 cells per lane -- built for 10 warps the same launches
-  // ran 8 % slower on the 1242-pixel row; 4 pixels and 20 warps (96
-  // registers) for the banded variant there, whose band bookkeeping would
+  // pixels per group and warps per CTA: 8 pixels and 8 warps (202 registers
+  // a thread) up to 8 cells per lane -- built for 10 warps it was held to 168
+  // registers and ran 8 % slower on the 1242-pixel row; 4 pixels and 20 warps
+  // (96 registers) for the banded variant there, whose band bookkeeping would
   // spill at 8; 4 pixels and 10 warps above 8 cells per lane
   static constexpr int P = CPL <= 8 && !BANDED ? 8 : 4;
   static constexpr int kMaxWarps = CPL <= 8 ? (BANDED ? 20 : 8) : 10;
