@@ -249,18 +249,25 @@ __global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ 
 // Column pass (van Herk / Gil-Werman): with the rows cut into blocks of
 // L = 2r + 1, the window [u, u + 2r] is the suffix OR of u's block from u
 // together with the prefix OR of (u + 2r)'s block up to u + 2r, so every
-// output costs O(1) whatever r.  A lane owns one column of kColT output rows,
-// the 32 lanes of a warp on consecutive x (every load is one coalesced row
-// segment).  It stages its kColT + 2r input rows in shared memory, many loads
-// in flight, then runs both scans there (its own column: no barrier).
-constexpr int kColT = 32;
+// output costs O(1) whatever r.  A lane owns one column, the 32 lanes of a
+// warp on consecutive x (every load is one coalesced row segment), and
+// streams kColSeg output rows from the kColSeg + 2r input rows above and
+// below them, each read once, loads kColChunk rows ahead.  Segments are
+// kColSeg rows, or down to kColSegMin for grids that would not fill the GPU
+// (few frames a call), whose CTAs re-read more halo rows but run in parallel.  It keeps two
+// blocks in shared memory: the raw rows of the block being read (its prefix
+// OR runs in a register) and, once a block is complete, its suffix ORs in
+// place.  Output i = u - 2r, read when row u arrives, lies in u's block (u at
+// the block's end, i at its start) or in the block before, so two buffers
+// alternating by block are enough.
+constexpr int kColSeg = 128, kColSegMin = 32, kColChunk = 8;
 
-__host__ __device__ constexpr int boxor_col_smem(int r) { return (2 * kColT + 2 * r) * 32 * 4; }
+__host__ __device__ constexpr int boxor_col_smem(int r) { return 2 * (2 * r + 1) * 32 * 4; }
 
 __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
                                                   uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
-                                                  int H, int MW, int rs, int rc) {
-  extern __shared__ uint32_t colbuf[];         // [kColT + 2r][32] inputs, then [kColT][32] suffix ORs
+                                                  int H, int MW, int rs, int rc, int seg) {
+  extern __shared__ uint32_t colbuf[];         // [2][L][32]: the two blocks, one word per lane
   const int lane = threadIdx.x;
   const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
   const uint32_t *src = which ? tmpC : tmpS;
@@ -268,51 +275,59 @@ __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ 
   const int r = which ? rc : rs;
   if (r < 0) return;                           // this radius is not wanted
   const size_t base = ((size_t)f * MW + w) * H * W;
-  const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * kColT;
-  const int L = 2 * r + 1, n = kColT + 2 * r, ylo = y0 - r;
-  uint32_t *in = colbuf + lane, *suf = colbuf + n * 32 + lane;
-  // input row u is image row ylo + u, zero outside the image
-  {
-    const int ua = max(0, -ylo), ub = x < W ? min(n, H - ylo) : 0;   // rows inside: [ua, ub)
-    const uint32_t *q = src + base + min(x, W - 1) + (ptrdiff_t)(ylo + ua) * W;
-    for (int u = 0; u < ua; ++u) in[u * 32] = 0u;
-#pragma unroll 16
-    for (int u = ua; u < ub; ++u, q += W) in[u * 32] = *q;
-    for (int u = max(ua, ub); u < n; ++u) in[u * 32] = 0u;
-  }
-  // suffix ORs within the blocks [kL, (k+1)L) of u, kept for u < kColT (a
-  // block end is at most u + 2r < n)
-  uint32_t acc = 0u;
-  int p = (n - 1) % L;                         // position of u in its block
-  int u = n - 1;
-  for (; u >= kColT; --u) {
-    if (p == L - 1) acc = 0u;
-    acc |= in[u * 32];
-    p = p == 0 ? L - 1 : p - 1;
-  }
-#pragma unroll 8
-  for (; u >= 0; --u) {
-    if (p == L - 1) acc = 0u;
-    acc |= in[u * 32];
-    suf[u * 32] = acc;
-    p = p == 0 ? L - 1 : p - 1;
-  }
-  // prefix ORs; out(y0 + i) = suffix(i) | prefix(i + 2r)
-  acc = 0u;
-  p = 0;
-  for (u = 0; u < 2 * r; ++u) {
-    if (p == 0) acc = 0u;
-    acc |= in[u * 32];
-    p = p == L - 1 ? 0 : p + 1;
-  }
-  const int nout = x < W ? min(kColT, H - y0) : 0;
+  const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * seg;
+  const int L = 2 * r + 1, T = min(seg, H - y0), n = T + 2 * r, ylo = y0 - r;
+  const bool live = x < W;
+  // lanes past the image's right edge read its last column and store nothing
+  const uint32_t *col = src + base + min(x, W - 1);
   uint32_t *o = dst + base + min(x, W - 1) + (size_t)y0 * W;
-#pragma unroll 8
-  for (int i = 0; i < kColT; ++i, ++u, o += W) {
-    if (p == 0) acc = 0u;
-    acc |= in[u * 32];
-    if (i < nout) *o = suf[i * 32] | acc;
-    p = p == L - 1 ? 0 : p + 1;
+  // input row u is image row ylo + u, zero outside the image
+  auto load = [&](int u) -> uint32_t {
+    const int y = ylo + u;
+    return u < n && y >= 0 && y < H ? col[(size_t)y * W] : 0u;
+  };
+  uint32_t nxt[kColChunk];
+#pragma unroll
+  for (int k = 0; k < kColChunk; ++k) nxt[k] = load(k);
+  uint32_t pre = 0u;                           // prefix OR of u's block up to u
+  int p = 0, kb = 0;                           // u's position in its block, the block's buffer
+  for (int u0 = 0; u0 < n; u0 += kColChunk) {
+    uint32_t cur[kColChunk];
+#pragma unroll
+    for (int k = 0; k < kColChunk; ++k) {
+      cur[k] = nxt[k];
+      nxt[k] = load(u0 + kColChunk + k);
+    }
+#pragma unroll
+    for (int k = 0; k < kColChunk; ++k) {
+      const int u = u0 + k;
+      if (u >= n) break;
+      uint32_t *b = colbuf + lane + (kb ? L * 32 : 0), *prev = colbuf + lane + (kb ? 0 : L * 32);
+      if (p == 0) pre = 0u;
+      pre |= cur[k];
+      b[p * 32] = cur[k];
+      if (p == L - 1) {
+        // the block is complete: its suffix ORs, in place
+        uint32_t sfx = 0u;
+#pragma unroll 4
+        for (int q = L - 1; q >= 0; --q) {
+          sfx |= b[q * 32];
+          b[q * 32] = sfx;
+        }
+      }
+      if (u >= 2 * r) {
+        // i = u - 2r sits at position p + 1 of the previous block, or at 0 of this one
+        const int i = u - 2 * r;
+        const uint32_t sfx = p == L - 1 ? b[0] : prev[(p + 1) * 32];
+        if (live) o[(size_t)i * W] = sfx | pre;
+      }
+      if (p == L - 1) {
+        p = 0;
+        kb ^= 1;
+      } else {
+        ++p;
+      }
+    }
   }
 }
 
@@ -339,16 +354,24 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static bool done[64] = {};
+  static int sms[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !done[dev]) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!done[dev]) {
     e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     done[dev] = true;
   }
-  // y: row tile x radius (bit 0), z: frame x word plane
-  dim3 g((k.W + 31) / 32, 2 * ((k.H + kColT - 1) / kColT), nf * k.MW);
-  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc);
+  // the longest segment whose grid still makes about two waves of one-warp
+  // CTAs (about 20 resident a SM at r = 20)
+  const long ctas_per_seg = (long)((k.W + 31) / 32) * 2 * nf * k.MW;
+  int seg = kColSeg;
+  while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms[dev]) seg /= 2;
+  // y: row segment x radius (bit 0), z: frame x word plane
+  dim3 g((k.W + 31) / 32, 2 * ((k.H + seg - 1) / seg), nf * k.MW);
+  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc, seg);
   return cudaGetLastError();
 }
 

@@ -75,3 +75,34 @@ def test_only_the_wanted_radius(gpu):
                 ctx.stage(other)
         finally:
             ctx.close()
+
+
+@pytest.mark.parametrize("n", [1, 20, 32])
+def test_box_masks_in_a_batch(gpu, n):
+    """Batches of 256 x 300 frames at D = 128: the column pass streams row
+    segments of 32, 64 or 128 rows, the longest whose grid still fills the
+    device (on 152 SMs these batch sizes give the three lengths).  Frame 0's
+    masks must equal the max filter; the outputs of the first, middle and
+    last frame, which go through both masks, must equal the oracle's."""
+    import torch
+    W, H, D = 256, 300, 128
+    scs = [scenes.random_small(9900 + i, W, H, D, density=0.08) for i in range(n)]
+    dev = torch.device("cuda:0")
+    ctx = S.Context(W, H, D, max_batch=n)
+    try:
+        out = torch.empty((n, H, W), dtype=torch.int16, device=dev)
+        ctx.compute(torch.from_numpy(np.stack([s.left for s in scs])).to(dev),
+                    torch.from_numpy(np.stack([s.right for s in scs])).to(dev),
+                    torch.from_numpy(np.stack([s.lidar for s in scs])).to(dev), out)
+        ctx.sync()
+        box_s, box_c = ctx.stage(S.SGMF_STAGE_BOX_S), ctx.stage(S.SGMF_STAGE_BOX_C)
+        got = out.cpu().numpy()
+    finally:
+        ctx.close()
+    dbar = oracle.lidar(scs[0].lidar, D)
+    np.testing.assert_array_equal(box_s, _want(dbar, D, 6), err_msg="r_s")
+    np.testing.assert_array_equal(box_c, _want(dbar, D, 20), err_msg="r_c")
+    for i in sorted({0, n // 2, n - 1}):
+        s = scs[i]
+        np.testing.assert_array_equal(got[i], oracle.compute(s.left, s.right, s.lidar, D, dumps=False).out,
+                                      err_msg=f"frame {i}")
