@@ -174,24 +174,44 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
   tc_fence_after();
   const uint32_t tmem = *slot;
   const uint32_t idesc = idesc_bf16(128, 32);
-  bool ok = true;
-  int phase = 0;
-  for (int it = 0; it < tiles && ok; ++it) {
-    const long long tile = (long long)blockIdx.x * tiles + it;
-    if (tile >= ntile) break;                                // CTA-uniform
-    const int tx = (int)(tile % tpr);
+  // the 16-byte pieces a thread stages: rows y-1, y, y+1, pixels x0-1 ..
+  // x0+128, four chunks each; all of a tile's loads are issued together, and
+  // the next tile's while this one's MMAs and epilogue run
+  constexpr int kPieces = 3 * kCvPix * 4, kPer = (kPieces + 127) / 128;
+  auto fetch = [&](long long tile, uint4 (&v)[kPer]) {
+    const int x0 = (int)(tile % tpr) * kCvM;
     const long long row = tile / tpr;                        // img * h + y
     const int y = (int)(row % a.h);
     const long long img = row / a.h;
-    const int x0 = tx * kCvM;
-    // stage rows y-1, y, y+1, pixels x0-1 .. x0+128, as chunk planes
-    for (int i = tid; i < 3 * kCvPix * 4; i += 128) {
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int i = tid + s * 128;
       const int j = i & 3, px = (i >> 2) % kCvPix, ky = (i >> 2) / kCvPix;
       const int yy = y + ky - 1, xx = x0 - 1 + px;
-      const bool in = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-      const long long q = in ? (img * a.h + yy) * a.w + xx : 0;
-      const uint4 v = in ? reinterpret_cast<const uint4 *>(a.x + q * kBnC)[j] : make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4 *>(Xs + (ky * 4 + j) * kCvPlane + px * 16) = v;
+      const bool in = i < kPieces && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+      v[s] = in ? reinterpret_cast<const uint4 *>(a.x + ((img * a.h + yy) * a.w + xx) * kBnC)[j]
+                : make_uint4(0, 0, 0, 0);
+    }
+  };
+  uint4 pf[kPer];
+  const long long tile0 = (long long)blockIdx.x * tiles;
+  if (tile0 < ntile) fetch(tile0, pf);
+  bool ok = true;
+  int phase = 0;
+  for (int it = 0; it < tiles && ok; ++it) {
+    const long long tile = tile0 + it;
+    if (tile >= ntile) break;                                // CTA-uniform
+    const int tx = (int)(tile % tpr);
+    const long long row = tile / tpr;                        // img * h + y
+    const int x0 = tx * kCvM;
+    // the staged rows as chunk planes
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int i = tid + s * 128;
+      if (i < kPieces) {
+        const int j = i & 3, px = (i >> 2) % kCvPix, ky = (i >> 2) / kCvPix;
+        *reinterpret_cast<uint4 *>(Xs + (ky * 4 + j) * kCvPlane + px * 16) = pf[s];
+      }
     }
     fence_async_smem();
     tc_fence_before();
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
       }
       umma_commit(bar);
     }
+    if (it + 1 < tiles && tile + 1 < ntile) fetch(tile + 1, pf);
     __syncwarp();
     const bool w_ok = mbar_wait_bounded(bar, (uint32_t)(phase & 1), kWaitLimit);
     ++phase;
