@@ -166,7 +166,19 @@ __global__ void __launch_bounds__(128) k_bn_conv(const __grid_constant__ BnConvA
     mbar_init(bar, 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < kBnB / 16; i += 128) reinterpret_cast<uint4 *>(Bs)[i] = a.packed[i];
+  {
+    // the packed weights, three loads a thread in flight at a time
+    constexpr int kPerThread = kBnB / 16 / 128;
+    static_assert(kBnB % (16 * 128) == 0 && kPerThread % 3 == 0, "the weights split evenly over the CTA");
+#pragma unroll 1
+    for (int s0 = 0; s0 < kPerThread; s0 += 3) {
+      uint4 wv[3];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) wv[s] = a.packed[tid + (s0 + s) * 128];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) reinterpret_cast<uint4 *>(Bs)[tid + (s0 + s) * 128] = wv[s];
+    }
+  }
   const int tpr = (a.w + kCvM - 1) / kCvM;                   // tiles per image row
   const long long ntile = (long long)a.n * a.h * tpr;
   tc_fence_before();
@@ -629,8 +641,14 @@ extern "C" sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, cons
                                     int relu, const uint16_t *mask, uint16_t *y, float *yf, int *err, void *stream) {
   if (n < 1 || h < 1 || w < 1 || !x || !packed || !err || (!y && !yf)) return SGMF_ERR_ARG;
   const long long ntile = (long long)n * h * ((w + kCvM - 1) / kCvM);
-  // about four CTAs per SM, each walking consecutive tiles with its weights staged once
-  const int tiles = (int)std::max<long long>(1, std::min<long long>(8, ntile / (4 * 152)));
+  // one wave of about four CTAs per SM, each walking consecutive tiles with
+  // its weights staged once
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_conv");
+  const long long slots = 4LL * std::max(sms, 1);
+  const int tiles = (int)std::max<long long>(1, std::min<long long>(32, (ntile + slots - 1) / slots));
   BnConvArgs a{n, h, w, x, reinterpret_cast<const uint4 *>(packed), bias, relu, mask, y, yf, err};
   k_bn_conv<<<(unsigned)((ntile + tiles - 1) / tiles), 128, kCvSmem, static_cast<cudaStream_t>(stream)>>>(a, tiles);
   return bn_launch(cudaGetLastError(), "sgmf_bn_conv");
