@@ -392,9 +392,15 @@ __global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b0) {
   const CT *cl = static_cast<const CT *>(b.censL);
   const CT *cr = static_cast<const CT *>(b.censR);
   const CT c = cl[p];
+  // the mask words (MW <= 8), all loads in flight before the first is used
+  uint32_t mw[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) mw[w] = w < k.MW ? b.boxS[w * plane + p] : 0u;
   int best_h = 0x7fffffff, best_d = -1;
-  for (int w = 0; w < k.MW && best_h > 0; ++w) {
-    uint32_t m = b.boxS[w * plane + p];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    if (w >= k.MW || best_h == 0) break;
+    uint32_t m = mw[w];
     while (m != 0u) {
       const int d = w * 32 + __ffs(m) - 1;
       m &= m - 1u;
