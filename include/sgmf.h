@@ -254,7 +254,8 @@ sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_t *band_lo,
  * and d-hat.  Its convolutions run on the tensor cores (BF16 operands, FP32
  * accumulation).  All pointers are DEVICE pointers; every call is
  * asynchronous on `stream` (NULL = legacy default stream) and returns
- * SGMF_ERR_ARG for bad sizes or NULL buffers.  Tensors are channel-last:
+ * SGMF_ERR_ARG for bad sizes or NULL buffers, SGMF_ERR_CUDA when a launch
+ * (or the device query that sizes its grid) fails.  Tensors are channel-last:
  * activations bf16 [n][h][w][32]; weights bf16 [co][ky][kx][ci] (32 x 3 x 3 x
  * 32); bias f32 [32].  `err` is a device int that a bounded wait sets to
  * SGMF_ERR_TIMEOUT (6). */
