@@ -459,10 +459,12 @@ out:
  *   L_r(p, d) = C(p, d) + min{ L_r(p-r, d), L_r(p-r, d-1) + P1,
  *                              L_r(p-r, d+1) + P1, m + P2 } - m,
  *   m = min over the band of p - r of L_r(p - r, k),
- * where a term L_r(p - r, d') is left out unless d' lies in the band of
- * p - r AND in the band of p: the previous pixel's costs are seen through
- * the current band, so at the band's ends d-1 and d+1 are absent as Eq. 2
- * leaves out d-1 at d = 0 (m still ranges over the whole band of p - r).
+ * where a term L_r(p - r, d') is left out when d' is outside the band of
+ * p - r (as Eq. 2 leaves out d-1 at d = 0).  This is Eq. 2 read as what it
+ * is, the exact dynamic program of the chain energy of Eq. 1: with the
+ * labels of every pixel restricted to its band, the best predecessor label
+ * of d is any label of the band of p - r, so d-1 and d+1 enter wherever
+ * they lie in the band of p - r, whether or not they lie in the band of p.
  * S(p, d) = sum_r L_r(p, d) on the band of
  * p; d*_p = argmin over the band of p; d'(x') = argmin over the d with
  * x' + d < W and d in the band of (x' + d, y) of S(x' + d, y, d), or invalid
@@ -496,10 +498,8 @@ void sgmfo_path_banded(int W, int H, int D, int B, const int16_t *lo, const int3
             for (int d = a; d < ae; ++d) {
                 int best = m + p2;
                 if (d >= b && d < be && lv[po + d] < best) best = lv[po + d];
-                if (d - 1 >= a && d - 1 >= b && d - 1 < be && lv[po + d - 1] + p1 < best)
-                    best = lv[po + d - 1] + p1;
-                if (d + 1 < ae && d + 1 >= b && d + 1 < be && lv[po + d + 1] + p1 < best)
-                    best = lv[po + d + 1] + p1;
+                if (d - 1 >= b && d - 1 < be && lv[po + d - 1] + p1 < best) best = lv[po + d - 1] + p1;
+                if (d + 1 >= b && d + 1 < be && lv[po + d + 1] + p1 < best) best = lv[po + d + 1] + p1;
                 lv[o + d] = cv[o + d] + best - m;
             }
         }

@@ -43,17 +43,16 @@ def test_constant_band_is_the_plain_method_on_a_slice(a0, B):
 
 
 def _brute_banded(C, bands, p1, p2):
-    """min over labelings with label_i in bands[i] of the chain energy, by final
-    label; a step of one disparity costs P1 only when the previous label is
-    also inside the current band (seen through it), else P2."""
+    """min over labelings with label_i in bands[i] of the chain energy of
+    Eq. 1 (P1 for a step of one disparity, P2 for a larger one), by final
+    label: the unmodified energy, only the label sets are restricted."""
     n, D = C.shape
     best = np.full(D, np.inf)
     for lab in itertools.product(*[range(a, b) for a, b in bands]):
         e = sum(int(C[i, lab[i]]) for i in range(n))
         for i in range(1, n):
             dd = abs(lab[i] - lab[i - 1])
-            seen = bands[i][0] <= lab[i - 1] < bands[i][1]
-            e += (p1 if seen else p2) if dd == 1 else (p2 if dd > 1 else 0)
+            e += p1 if dd == 1 else (p2 if dd > 1 else 0)
         best[lab[-1]] = min(best[lab[-1]], e)
     return best
 
@@ -109,3 +108,22 @@ def test_banded_right_view_search_none_inside():
     # x'=0: (0,0) below the band {1} of x=0, (1,1) and (2,2) above the bands {0}
     assert dp[0, 0] == -1
     assert dp[0, 1] == 0 and dp[0, 2] == 0
+
+
+def test_banded_step_into_a_shifted_band_hand_case():
+    """A neighbour disparity that lies in the previous pixel's band but below
+    the current one still enters Eq. 2 with P1: the best chain into label 1
+    of the second pixel comes from label 0 of the first (cost P1), a label
+    the second pixel's band [1, 3) does not hold."""
+    p1, p2 = 3, 20
+    cv = np.array([[[0, 50, 50], [9, 4, 50]]], np.int32)
+    lo = np.array([[0, 1]], np.int16)
+    L = oracle.path_banded(cv, lo, 2, p1, p2, 1, 0)[0]
+    # first pixel: band [0, 2), L = C
+    assert L[0, 0] == 0 and L[0, 1] == 50 and L[0, 2] == oracle.ABSENT
+    # second pixel, m = 0: d = 1: 4 + min(50, 0 + P1, 0 + P2) = 7;
+    # d = 2: 50 + min(absent, 50 + P1, 0 + P2) = 70
+    assert L[1, 0] == oracle.ABSENT and L[1, 1] == 4 + p1 and L[1, 2] == 50 + p2
+    # the same by brute force over the two labelings of each final label
+    want = _brute_banded(cv[0], [(0, 2), (1, 3)], p1, p2)
+    assert want[1] == L[1, 1] and want[2] == L[1, 2]

@@ -460,6 +460,79 @@ def test_consistency_predicate_symmetry():
         assert (o1[2, 2] >= 0) == (o2[2, 2] >= 0) == (abs(a - b) <= t)
 
 
+def _right_view_check(dstar, dprime, lr):
+    """The stereo condition of Eq. 6 seen from the right view, by direct
+    loops: right pixel x' keeps d'(x') when its match x' + d'(x') lies in
+    the image and |d'(x') - d*(x' + d'(x'))| <= lr."""
+    H, W = dstar.shape
+    out = np.full((H, W), -1, np.int16)
+    for y in range(H):
+        for xr in range(W):
+            d = int(dprime[y, xr])
+            x = xr + d
+            if 0 <= d and x < W and abs(d - int(dstar[y, x])) <= lr:
+                out[y, xr] = d
+    return out
+
+
+def _consistent_maps(rng, H, W, D, jitter):
+    """A left map d* of slanted planes (slope in [0, 1/2), no occlusion) and
+    the right map d' it induces (x' = x - d*(x)), plus optional random
+    jitter of d' in [-jitter, jitter]."""
+    ds = np.zeros((H, W), np.int16)
+    dp = np.zeros((H, W), np.int16)
+    for y in range(H):
+        a, b = rng.uniform(1, D // 2), rng.uniform(0.0, 0.49)
+        row = np.minimum(np.rint(a + b * np.arange(W)), D - 1).astype(np.int64)
+        ds[y] = row
+        dp[y] = row[-1] if W else 0
+        for x in range(W - 1, -1, -1):       # the leftmost x of each x' wins, as any would
+            if x - row[x] >= 0:
+                dp[y, x - row[x]] = row[x]
+        if jitter:
+            dp[y] = np.clip(dp[y] + rng.integers(-jitter, jitter + 1, size=W), 0, D - 1)
+    return ds, dp
+
+
+@pytest.mark.parametrize("lr", [0, 1, 2])
+def test_consistency_mirror_identity(lr):
+    """P-6(ii): the L-R check of Eq. 6 run with the views swapped and
+    mirrored horizontally (the right map as d*, the left map as d', both
+    mirrored) equals the check from the right view, mirrored back.  The
+    maps are near-consistent (d' jittered by up to 2), so that a lookup of
+    d' one pixel off q_m = (x - d*, y) changes many decisions."""
+    rng = np.random.default_rng(60 + lr)
+    for _ in range(6):
+        H, W, D = int(rng.integers(1, 6)), int(rng.integers(8, 60)), int(rng.integers(4, 40))
+        ds, dp = _consistent_maps(rng, H, W, D, 2)
+        none = np.full((H, W), -1, np.int16)
+        swapped = oracle.consistency(dp[:, ::-1], ds[:, ::-1], none, 2, 20, lr, oracle.CHECK_STEREO)
+        np.testing.assert_array_equal(swapped[:, ::-1], _right_view_check(ds, dp, lr))
+
+
+def test_consistency_passes_everywhere_on_consistent_maps():
+    """P-6(ii): on occlusion-free, mutually consistent maps the L-R check
+    keeps every pixel whose match lies in the image, and so does the check
+    from the right view (for every right pixel that some left pixel maps to)."""
+    rng = np.random.default_rng(66)
+    for _ in range(6):
+        H, W, D = 4, int(rng.integers(16, 80)), int(rng.integers(4, 40))
+        ds, dp = _consistent_maps(rng, H, W, D, 0)
+        none = np.full((H, W), -1, np.int16)
+        out = oracle.consistency(ds, dp, none, 2, 20, 1, oracle.CHECK_STEREO)
+        xs = np.arange(W)[None, :]
+        inside = xs - ds >= 0
+        np.testing.assert_array_equal(out[inside], ds[inside])
+        assert (out[~inside] == -1).all()
+        rv = _right_view_check(ds, dp, 1)
+        hit = np.zeros((H, W), bool)
+        for y in range(H):
+            for x in range(W):
+                if x - ds[y, x] >= 0:
+                    hit[y, x - ds[y, x]] = True
+        np.testing.assert_array_equal(rv[hit], dp[hit])
+
+
 def test_consistency_uses_raw_sparse_map():
     s = scenes.tiny()
     r = oracle.compute(s.left, s.right, s.lidar, s.D)
