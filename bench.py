@@ -75,6 +75,35 @@ def algorithmic(name: str, V: int, N: int, num_paths: int = 8, sweep: bool = Fal
     return None
 
 
+# Whole-pipeline integer work per cell (V = W*H*D cells): 74 scalar 16-bit
+# operations (8 per cell and direction of Eq. 2 over 8 directions, 8 adds of
+# the path sum, 2 WTA mins) = 37 u16x2 instructions, plus the XOR and the
+# population count of the Hamming cost.  The u16x2 instructions and the XOR
+# are charged at the measured issue rate of the u16x2 3-input min (the rate
+# of the path recursion's min; plain 32-bit adds issue faster, so this is the
+# slower of the two ALU rates), the population count at its own rate.
+PIPE_U16X2_PER_CELL = 37
+PIPE_XOR_PER_CELL = 1
+PIPE_POPC_PER_CELL = 1
+
+
+def pipeline_roofline(rates: dict, sm_mhz: float, hbm_gbs: float, V: int, N: int, step_s: float) -> dict:
+    clk = sm_mhz * 1e6
+    r_alu = rates["min3_u16x2"] * rates["sms"] * clk          # u16x2 instructions per second
+    r_popc = rates["popc"] * rates["sms"] * clk
+    t_ops = V * ((PIPE_U16X2_PER_CELL + PIPE_XOR_PER_CELL) / r_alu + PIPE_POPC_PER_CELL / r_popc)
+    bytes_alg = 2 * V + 8 * N                                # u8 cost volume written and read once; images, LiDAR, output
+    t_bytes = bytes_alg / (hbm_gbs * 1e9)
+    bound = "alu" if t_ops >= t_bytes else "hbm"
+    return {"bound": bound, "ideal_s": max(t_ops, t_bytes), "t_ops_s": t_ops, "t_bytes_s": t_bytes,
+            "step_s": step_s, "frac": max(t_ops, t_bytes) / step_s,
+            "rates_lanes_per_clk_per_sm": {k: round(v, 2) for k, v in rates.items() if k != "sms"},
+            "sms": rates["sms"], "sm_mhz": sm_mhz,
+            "per_cell": {"u16x2": PIPE_U16X2_PER_CELL, "xor": PIPE_XOR_PER_CELL, "popc": PIPE_POPC_PER_CELL},
+            "note": "ideal = V x ((37 u16x2 + 1 xor) / u16x2-min rate + 1 / popc rate), rates from "
+                    "sgmf_measure_rates on this GPU, x SMs x the sampled SM clock; frac = ideal / step time"}
+
+
 # csrc files whose contents decide each timed kernel's code and launch shape
 # (the shared header and the API file that sizes the buffers go with every one)
 KERNEL_SOURCES = {
@@ -649,6 +678,13 @@ def main():
                     iso_times.setdefault(name, []).append(ms)
         sgmf.sgmf_set_tuning(ctx.handle, cur.line_warps, cur.cost_px, cur.sweep, 1)
 
+    # instruction rates of this device (lanes per clock per SM), for the pipeline roofline
+    try:
+        rates = sgmf.sgmf_measure_rates(256)
+    except Exception as e:          # reported, not fatal to the headline measurement
+        rates = None
+        print(f"rate probe failed: {e}", file=sys.stderr)
+
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if pg:
         import torch.distributed as dist
@@ -791,6 +827,13 @@ def main():
                              "frac": alg["ops"] / t_iso / alu_peak,
                              "note": "the same launches with parts off (the GPU to itself), 3 steps after the "
                                      "timed region; frac above is inside the timed pipeline"}
+
+    # whole-pipeline roofline: the method's integer work per cell at the
+    # instruction rates measured on this device by the library's probe
+    # kernel, and its algorithmic bytes at the measured copy bandwidth
+    if roof is not None and rates is not None:
+        roof["pipeline"] = pipeline_roofline(rates, sm_mhz, peaks["hbm_gbs"], V, N, total_ms / args.steps * 1e-3)
+        roof["pipeline_frac"] = roof["pipeline"]["frac"]
 
     cpu = None
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world > 1 and False):

@@ -216,6 +216,49 @@ sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n
 /* Bytes of device memory the context holds. */
 size_t sgmf_device_bytes(const sgmf_ctx *c);
 
+/* ---- Failure handling (no counterpart in the paper) ---------------------
+ * Every device wait of the library (TMA and bulk copies into shared memory,
+ * the cluster sweep's messages) polls a bounded number of times.  A wait
+ * that gives up records SGMF_ERR_TIMEOUT in the context's error word, waits
+ * again (with the default limit) for the copies its CTA issued, and returns:
+ * nothing faults, the context stays usable, and sgmf_sync reports
+ * SGMF_ERR_TIMEOUT (the outputs of that call are then undefined). */
+#define SGMF_WAIT_CENSUS 0   /* the census kernel's wait for its TMA image tiles */
+
+/* Poll limit of one kind of device wait of c (which = SGMF_WAIT_CENSUS):
+ * polls >= 0 sets it (0 gives up before the first poll, so every census CTA
+ * takes the timeout path: this is how the tests reach it), polls < 0
+ * restores the default 2^22.  Applies to the following computes.
+ * Errors: SGMF_ERR_ARG (NULL c, unknown wait). */
+sgmf_status sgmf_set_wait_limit(sgmf_ctx *c, int which, long long polls);
+
+/* ---- Instruction rates (no counterpart in the paper) ----------------------
+ * The integer path's roofline needs the rates at which the device issues the
+ * instructions the method is made of.  Lanes per clock per SM of each kind,
+ * measured on the current device by one CTA of 1024 threads per SM, eight
+ * independent chains a thread, iters x 16 steps a chain, timed by the CTA's
+ * clock64 span (the median CTA); independent of the SM clock. */
+typedef struct {
+  int sms;               /* SMs of the device                              */
+  double min3_u16x2;     /* __vimin3_u16x2: 3-input min of two u16 halves  */
+  double addmin_u16x2;   /* __viaddmin_u16x2: min(a + b, c) per u16 half   */
+  double iadd;           /* 32-bit add                                     */
+  double popc;           /* __popc (population count)                      */
+  double prmt;           /* __byte_perm                                    */
+} sgmf_rates;
+
+/* Run the probes (synchronises the device; a few ms at iters = 256).
+ * Errors: SGMF_ERR_ARG (out NULL, iters outside [1, 2^20]), SGMF_ERR_CUDA. */
+sgmf_status sgmf_measure_rates(int iters, sgmf_rates *out);
+
+/* Test hook for allocation failure: on the calling thread, the n-th device
+ * allocation that a context makes from now on (n >= 1) fails as if the
+ * device were out of memory, without calling cudaMalloc; n <= 0 clears it.
+ * The failing call (sgmf_create*, or the first sgmf_compute_host* or
+ * sgmf_set_debug that allocates) returns SGMF_ERR_OOM and keeps nothing it
+ * allocated: a failed sgmf_create frees every buffer it had obtained. */
+void sgmf_debug_fail_alloc(int n);
+
 /* ---- Banded mode (no counterpart in the paper) ---------------------------
  * The method restricted to a disparity band per pixel: pixel p keeps the
  * disparities [lo_p, lo_p + band); lo_p is constant on 8 x 8 pixel tiles.
@@ -474,8 +517,9 @@ void sgmf_server_destroy(sgmf_server *s);
  * (a pool they do not own, a real-time loop that forbids cudaMalloc after
  * start-up, a plugin host that only hands out input and output buffers).
  *
- * Computes D^{c*} of Eq. 6 for one width x height frame, exactly as
- * sgmf_compute's last stage does, from caller-owned DEVICE buffers: dstar and
+ * Gives the same output as sgmf_compute's consistency stage for the same
+ * d*, d' and LiDAR map, for one width x height frame, from caller-owned
+ * DEVICE buffers: dstar and
  * dprime (int16 H x W, d* and d' of the frame, e.g. SGMF_STAGE_DSTAR /
  * SGMF_STAGE_DPRIME), sparse_lidar_disp (float32 H x W, the same LiDAR map
  * given to sgmf_compute, or NULL) and out_disp (int16 H x W).  p supplies
@@ -489,8 +533,9 @@ void sgmf_server_destroy(sgmf_server *s);
  * a frame needs 3 * W * H * ceil(max_disp / 64) * 2 words (for max_disp <= 128
  * about 700 000 pixels fit).  Larger frames are rejected with SGMF_ERR_SHAPE
  * before anything is launched.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * (and again if the device's context was made anew, e.g. after
+ * cudaDeviceReset); make that first call before any stream capture.  All calls share the
  * array: calls that overlap on the GPU race.  No cudaMalloc, cudaFree or
  * allocating library call is made.  Errors: SGMF_ERR_ARG, SGMF_ERR_SHAPE,
  * SGMF_ERR_PARAM, SGMF_ERR_CUDA; the message is in sgmf_last_error(NULL). */

@@ -168,13 +168,14 @@ struct StepConsts {
 // halves; edge_lo / edge_hi are all-ones on the first / last lane of the
 // group so that the missing neighbours L(-1) and L(Dp) read as 0xffff (they
 // only enter a min).
+// The step proper, given the word below the lane's first cell (prev: its
+// high half is L(d-1) of the first cell) and the word above its last cell
+// (next: its low half is L(d+1) of the last cell).
 template <int NW>
-__device__ __forceinline__ void sgm_step(uint32_t (&L)[NW], const uint32_t (&C)[NW], uint32_t mm,
-                                         const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi) {
+__device__ __forceinline__ void sgm_core(uint32_t (&L)[NW], const uint32_t (&C)[NW], uint32_t mm,
+                                         const StepConsts &sc, uint32_t prev, uint32_t next) {
   const uint32_t cap = mm + sc.dpx2;           // m + P2 - P1 per half
   const uint32_t negmm = 0u - mm;
-  const uint32_t prev = __shfl_up_sync(kFull, L[NW - 1], 1, 16) | edge_lo;
-  const uint32_t next = __shfl_down_sync(kFull, L[0], 1, 16) | edge_hi;
   uint32_t sh[NW + 1];
   sh[0] = prmt(prev, L[0], 0x5432);
 #pragma unroll
@@ -185,6 +186,28 @@ __device__ __forceinline__ void sgm_step(uint32_t (&L)[NW], const uint32_t (&C)[
     const uint32_t t = __viaddmin_u16x2(__vimin3_u16x2(sh[i], sh[i + 1], cap), sc.p1x2, L[i]);
     L[i] = t + C[i] + negmm;
   }
+}
+
+template <int NW>
+__device__ __forceinline__ void sgm_step(uint32_t (&L)[NW], const uint32_t (&C)[NW], uint32_t mm,
+                                         const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi) {
+  const uint32_t prev = __shfl_up_sync(kFull, L[NW - 1], 1, 16) | edge_lo;
+  const uint32_t next = __shfl_down_sync(kFull, L[0], 1, 16) | edge_hi;
+  sgm_core<NW>(L, C, mm, sc, prev, next);
+}
+
+// The step of the banded walks.  On the group's end lanes the missing
+// neighbour is the lane's edge word e instead of all ones: lane 0 takes
+// L(d-1) of its first cell from the high half of e, lane 15 L(d+1) of its
+// last cell from the low half.  It is all ones (absent) except on the first
+// step after a band change, where it holds the previous pixel's cell just
+// outside the current band (band_shift).
+template <int NW>
+__device__ __forceinline__ void sgm_step_e(uint32_t (&L)[NW], const uint32_t (&C)[NW], uint32_t mm,
+                                           const StepConsts &sc, uint32_t e, int lig) {
+  const uint32_t up = __shfl_up_sync(kFull, L[NW - 1], 1, 16);
+  const uint32_t dn = __shfl_down_sync(kFull, L[0], 1, 16);
+  sgm_core<NW>(L, C, mm, sc, lig == 0 ? e : up, lig == 15 ? e : dn);
 }
 
 // Min of a u32 over each 16-lane group: two full-warp reductions, each with
@@ -227,7 +250,12 @@ __device__ __forceinline__ void pad_bytes(int D, int lig, uint32_t (&z)[CPL / 4]
 // pixel's path costs are re-indexed: cell j takes old cell j + delta, and the
 // cells that have no old counterpart become absent (kInf, above every real
 // path cost, so they only ever lose a min).  m of the previous pixel stays
-// the min over its own band, as the banded recursion requires.
+// the min over its own band.  The recursion on the bands is the exact
+// dynamic program of Eq. 1 with each pixel's labels restricted to its band,
+// so the previous pixel's cell just below the new band (old cell delta - 1,
+// for delta > 0) or just above it (old cell B + delta, for delta < 0) is
+// still the d-1 / d+1 neighbour of the new band's end cell: the shift hands
+// it to the next step in the end lane's edge word.
 struct BandState {
   const int16_t *lo = nullptr;   // this frame's tile table [th][tw]
   int tw = 0;
@@ -241,8 +269,12 @@ struct BandState {
 // Runs on all 32 lanes (full-warp syncs): a group with delta = 0 rewrites its
 // cells in place.  Keeping the shift warp-uniform matters: the recursion's
 // full-warp reductions must never meet a group parked at a partial barrier.
+// edge receives the lane's edge word for the next step (sgm_step_e): on lane
+// 0 the old cell delta - 1 in the high half, on lane 15 the old cell
+// B + delta in the low half, all ones where that cell is outside the old band.
 template <int CPL>
-__device__ __forceinline__ void band_shift(uint32_t (&L)[CPL / 2], int delta, uint16_t *buf, int lig) {
+__device__ __forceinline__ void band_shift(uint32_t (&L)[CPL / 2], int delta, uint16_t *buf, int lig,
+                                           uint32_t &edge) {
   constexpr int NW = CPL / 2, B = 16 * CPL;
   uint32_t *w = reinterpret_cast<uint32_t *>(buf + lig * CPL);
 #pragma unroll
@@ -255,14 +287,19 @@ __device__ __forceinline__ void band_shift(uint32_t (&L)[CPL / 2], int delta, ui
     const uint32_t v1 = (unsigned)(c0 + 1) < (unsigned)B ? (uint32_t)buf[c0 + 1] : kInf;
     L[i] = v0 | (v1 << 16);
   }
+  const int ce = lig == 0 ? delta - 1 : B + delta;
+  const uint32_t ve = (unsigned)ce < (unsigned)B ? (uint32_t)buf[ce] : 0xffffu;
+  edge = lig == 0 ? (ve << 16) | 0xffffu : 0xffff0000u | ve;
   __syncwarp();
 }
 
 // the band bookkeeping of one step at (bs.x, bs.y), then the move to the next
 // pixel of the line (x wraps for the diagonals).  Called by all 32 lanes;
-// returns the change of the band start (0 for an inactive lane).
+// returns the change of the band start (0 for an inactive lane) and sets the
+// lane's edge word for this step's recursion (all ones without a shift).
 template <int CPL>
-__device__ __forceinline__ int band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig) {
+__device__ __forceinline__ int band_step(BandState &bs, uint32_t (&L)[CPL / 2], bool active, int W, int lig,
+                                         uint32_t &edge) {
   int delta = 0;
   if (active) {
     const int t = (bs.y >> kBandTileLog) * bs.tw + (bs.x >> kBandTileLog);
@@ -273,7 +310,8 @@ __device__ __forceinline__ int band_step(BandState &bs, uint32_t (&L)[CPL / 2], 
       bs.cur = nlo;
     }
   }
-  if (__any_sync(kFull, delta != 0)) band_shift<CPL>(L, delta, bs.buf, lig);
+  edge = 0xffffffffu;
+  if (__any_sync(kFull, delta != 0)) band_shift<CPL>(L, delta, bs.buf, lig, edge);
   bs.y += bs.dy;
   bs.x += bs.dx;
   bs.x = bs.x >= W ? bs.x - W : (bs.x < 0 ? bs.x + W : bs.x);
@@ -383,7 +421,8 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
   for (int i = 0; i < n; ++i) {
     const int r = DOWN ? i : n - 1 - i;       // stage rows are in increasing y
     unpack_u8<CPL>(stl + r * 2 * Dp, z, C);
-    if (BANDED) band_step<CPL>(bs, L, active, W, lig);
+    uint32_t edge = 0xffffffffu;
+    if (BANDED) band_step<CPL>(bs, L, active, W, lig, edge);
     if (!FAST) {
       const bool start = togo == 0;
       const uint32_t keep = start ? 0u : 0xffffffffu;
@@ -407,7 +446,10 @@ __device__ __forceinline__ void line_chunk(const uint8_t *stl, const uint8_t *ss
       }
       --togo;
     }
-    sgm_step<NW>(L, C, mm, sc, edge_lo, edge_hi);
+    if constexpr (BANDED)
+      sgm_step_e<NW>(L, C, mm, sc, edge, lig);
+    else
+      sgm_step<NW>(L, C, mm, sc, edge_lo, edge_hi);
     mm = group_min<NW>(L, grp);
     if constexpr (S8) {
       // this direction's path costs, one byte per cell, in its half of the pixel's slot
@@ -650,9 +692,10 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
     uint32_t C[NW];
     unpack_u8<CPL>(cst + r * Dp, z, C);
     int delta = 0;
+    uint32_t edge = 0xffffffffu;
     if (BANDED) {
       bs.x = x;   // rows: the tile follows x (bs.y is the row)
-      delta = band_step<CPL>(bs, w.L, valid, g.W, lig);
+      delta = band_step<CPL>(bs, w.L, valid, g.W, lig, edge);
       if (SECOND && bs.cur != bs.kb_lo) {
         // keys carry absolute disparities: lo + slot
         bs.kb_lo = bs.cur;
@@ -668,7 +711,10 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
       for (int i = 0; i < NW; ++i) w.L[i] &= keep;
       w.mm &= keep;
     }
-    sgm_step<NW>(w.L, C, w.mm, sc, edge_lo, edge_hi);
+    if constexpr (BANDED)
+      sgm_step_e<NW>(w.L, C, w.mm, sc, edge, lig);
+    else
+      sgm_step<NW>(w.L, C, w.mm, sc, edge_lo, edge_hi);
     w.mm = group_min<NW>(w.L, grp);
     if (!SECOND) {
       if (valid) spill_put<CPL, S8>(spill_lane + (size_t)x * Dp * SB, w.L);
@@ -993,12 +1039,9 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
 // opt in once per device to the kernel's dynamic shared memory
 template <typename Kern>
 static cudaError_t smem_optin(Kern kern, int bytes, bool (&done)[64]) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
-  return e;
+  return once_per_device(done, [&](int) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
 }
 
 template <int CPL, bool S8, int FAM, int NWARP, bool BANDED>

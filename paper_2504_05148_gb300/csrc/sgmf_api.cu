@@ -31,29 +31,50 @@ struct sgmf_ctx {
   bool sweep_ok = false;       // the row-synchronous sweep can run this shape on this device (8 paths)
   int sweep_slots = 0;         // sweep clusters the device holds at once
   size_t spill_bytes = 0;
-  // with the sweep, a batch goes through in parts: each part's row kernel
-  // runs on this second stream while the next part is in the sweep
+  // with the sweep, a batch goes through in parts: part i's sweep runs on
+  // the context's stream while part i+1's front stages (ingest .. cost) run
+  // on `front` and part i's row kernel and check on `side`
   static constexpr int kMaxParts = 8;
-  cudaStream_t side = nullptr;
+  cudaStream_t side = nullptr, front = nullptr;
   cudaEvent_t ev_part[kMaxParts] = {};
-  cudaEvent_t ev_rows = nullptr;
+  cudaEvent_t ev_front[kMaxParts] = {};
+  cudaEvent_t ev_rows = nullptr, ev_in = nullptr;
   size_t bytes = 0;
   std::string err;
   // device staging for sgmf_compute_host
   uint8_t *st_left = nullptr, *st_right = nullptr;
   float *st_lidar = nullptr;
   int16_t *st_out = nullptr;
-  // profiling
+  // profiling: an event pair around every launch, on the launching stream
+  struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+  };
   bool profiling = false;
-  std::vector<cudaEvent_t> ev;
-  std::vector<const char *> names;
-  int nrec = 0;
+  std::vector<cudaEvent_t> ev;     // pool, reused by every compute
+  int evused = 0;
+  std::vector<ProfRec> recs;
   bool computed = false;
   int last_n = 0;
   bool debug = false;
 };
 
 static thread_local std::string g_create_err;
+
+std::mutex &sgmf::setup_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+cudaError_t sgmf::sm_count(int *out) {
+  static bool done[64] = {};
+  static int sms[64] = {};
+  int dev = 0;
+  cudaError_t e = once_per_device(done, [](int d) { return cudaDeviceGetAttribute(&sms[d], cudaDevAttrMultiProcessorCount, d); });
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) *out = sms[dev];
+  return e;
+}
 
 static sgmf_status fail(sgmf_ctx *c, sgmf_status s, const char *fmt, ...) {
   char buf[512];
@@ -184,18 +205,32 @@ static void free_all(sgmf_ctx *c) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
-  for (cudaEvent_t &e : c->ev_part) {
-    if (e) cudaEventDestroy(e);
-    e = nullptr;
+  for (cudaEvent_t *arr : {c->ev_part, c->ev_front})
+    for (int i = 0; i < sgmf_ctx::kMaxParts; ++i) {
+      if (arr[i]) cudaEventDestroy(arr[i]);
+      arr[i] = nullptr;
+    }
+  for (cudaEvent_t *e : {&c->ev_rows, &c->ev_in}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
   }
-  if (c->ev_rows) cudaEventDestroy(c->ev_rows);
-  if (c->side) cudaStreamDestroy(c->side);
-  c->ev_rows = nullptr;
-  c->side = nullptr;
+  for (cudaStream_t *st : {&c->side, &c->front}) {
+    if (*st) cudaStreamDestroy(*st);
+    *st = nullptr;
+  }
 }
+
+// test hook (sgmf_debug_fail_alloc): allocations until the injected failure
+static thread_local int g_fail_alloc = 0;
+
+extern "C" void sgmf_debug_fail_alloc(int n) { g_fail_alloc = n > 0 ? n : 0; }
 
 template <typename T>
 static cudaError_t dalloc(sgmf_ctx *c, T **p, size_t bytes) {
+  if (g_fail_alloc > 0 && --g_fail_alloc == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;     // injected: cudaMalloc is not called
+  }
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
   if (e == cudaSuccess) c->bytes += bytes;
   return e;
@@ -235,6 +270,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   k.pitch = (width + 15) / 16 * 16;
   k.line_warps = 4;
   k.cost_px = 128;
+  k.wait_census = kWaitLimit;
   k.sweep = 0;
   k.parts = 1;
   sgmf_params def;
@@ -291,9 +327,12 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     c->sweep_ok = c->k.sweep_cs > 0;
     bool ok = !(c->sweep_ok && c->nb >= 2) ||
               (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
-               cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) == cudaSuccess);
+               cudaStreamCreateWithFlags(&c->front, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess);
     for (int i = 0; ok && c->side && i < sgmf_ctx::kMaxParts; ++i)
-      ok = cudaEventCreateWithFlags(&c->ev_part[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = cudaEventCreateWithFlags(&c->ev_part[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->ev_front[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       c->sweep_slots = 0;        // no parts: everything on the context's stream
@@ -349,6 +388,13 @@ extern "C" sgmf_status sgmf_get_params(const sgmf_ctx *c, sgmf_params *p) {
   return SGMF_OK;
 }
 
+extern "C" sgmf_status sgmf_set_wait_limit(sgmf_ctx *c, int which, long long polls) {
+  if (!c) return SGMF_ERR_ARG;
+  if (which != SGMF_WAIT_CENSUS) return fail(c, SGMF_ERR_ARG, "sgmf_set_wait_limit: unknown wait %d", which);
+  c->k.wait_census = polls < 0 ? kWaitLimit : (uint32_t)std::min<long long>(polls, 0xffffffffLL);
+  return SGMF_OK;
+}
+
 extern "C" sgmf_status sgmf_set_stream(sgmf_ctx *c, void *stream) {
   if (!c) return SGMF_ERR_ARG;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -361,11 +407,12 @@ static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STE
 static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths == 8 && c->sweep_ok; }
 
 // Frames per part when a sweep batch of n frames goes through in parts (0:
-// one part).  A part's row kernel runs on the side stream beside the next
-// part's sweep, filling the SMs (and the register room) the sweep clusters
-// leave.  Every part but the last is one wave of sweep clusters (2 m
-// cluster jobs, the resident count or its smallest even multiple), so the
-// parts add no wave; at most kMaxParts parts.
+// one part).  A part's row kernel and check run on the side stream, and the
+// next part's front stages on the front stream, beside the part's sweep:
+// they fill the SMs (and the register room) the sweep clusters leave, and
+// the next sweep finds its cost volume ready.  Every part but the last is
+// one wave of sweep clusters (2 m cluster jobs, the resident count or its
+// smallest even multiple), so the parts add no wave; at most kMaxParts parts.
 static int sweep_part(const sgmf_ctx *c, int n) {
   if (!c->k.parts || !c->side || c->sweep_slots < 1 || n < 2) return 0;
   int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 m % slots == 0
@@ -381,33 +428,54 @@ static KParams agg_params(const sgmf_ctx *c) {
   return k;
 }
 
-extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
-  if (!c) return 0;
-  // ingest, census, cost, rows + one line launch per family (one sweep launch for all six directions)
-  // (a sweep batch in parts launches the sweep and the row kernel once per part; counted for a full batch)
-  int n = 4 + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1);
-  if (use_sweep(c) && sweep_part(c, c->nb) > 0) {
-    const int m = sweep_part(c, c->nb), parts = (c->nb + m - 1) / m;
-    n += 2 * (parts - 1);
-  }
-  if (c->k.semidense || need_boxc(c->k)) n += 2;   // box-OR rows and columns, both radii
-  if (c->k.semidense) n += 1;
-  n += 1;      // consistency
-  if (c->k.band) n += 1;   // band clamp
-  return n;
+// launches of the front stages (ingest, census, box-OR rows and columns, semidense, cost)
+static int front_launches(const KParams &k) {
+  return 3 + ((k.semidense || need_boxc(k)) ? 2 : 0) + (k.semidense ? 1 : 0);
 }
 
-static void mark(sgmf_ctx *c, const char *name) {
-  if (!c->profiling) return;
-  if (c->nrec >= (int)c->ev.size()) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return;
-    c->ev.push_back(e);
-    c->names.push_back(nullptr);
+extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
+  if (!c) return 0;
+  // front stages, one line launch per family (one sweep launch for all six directions), rows, consistency
+  // (a sweep batch in parts launches all of them once per part; counted for a full batch)
+  const int per = front_launches(c->k) + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1) + 2;
+  int parts = 1;
+  if (use_sweep(c) && sweep_part(c, c->nb) > 0) {
+    const int m = sweep_part(c, c->nb);
+    parts = (c->nb + m - 1) / m;
   }
-  c->names[c->nrec] = name;
-  cudaEventRecord(c->ev[c->nrec], c->stream);
-  ++c->nrec;
+  return per * parts + (c->k.band ? 1 : 0);   // + band clamp
+}
+
+// an event of the pool (null when none can be created: that launch goes untimed)
+static cudaEvent_t prof_event(sgmf_ctx *c) {
+  if (c->evused >= (int)c->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    c->ev.push_back(e);
+  }
+  return c->ev[c->evused++];
+}
+
+// start / end of a timed launch on stream s (profiling on)
+static int prof_begin(sgmf_ctx *c, const char *name, cudaStream_t s) {
+  if (!c->profiling) return -1;
+  cudaEvent_t a = prof_event(c), b = prof_event(c);
+  if (!a || !b) return -1;
+  cudaEventRecord(a, s);
+  c->recs.push_back({name, a, b});
+  return (int)c->recs.size() - 1;
+}
+
+static void prof_end(sgmf_ctx *c, int r, cudaStream_t s) {
+  if (r >= 0) cudaEventRecord(c->recs[r].b, s);
+}
+
+static void prof_reset(sgmf_ctx *c) {
+  c->recs.clear();
+  c->evused = 0;
 }
 
 #define LAUNCH_TRY(c, call)                                                          \
@@ -417,6 +485,35 @@ static void mark(sgmf_ctx *c, const char *name) {
       return fail((c), SGMF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
+// a launch between the events of one profiling record
+#define TIMED(c, name, s, call)                     \
+  do {                                              \
+    const int r_ = prof_begin((c), (name), (s));    \
+    LAUNCH_TRY((c), (call));                        \
+    prof_end((c), r_, (s));                         \
+  } while (0)
+
+// The stages before aggregation (ingest, census, box-OR, semidense and,
+// with `cost`, the cost volume) for frames [f0, f0 + nf) on stream s; the
+// inputs are the call's frame-0 pointers.
+static sgmf_status front_stages(sgmf_ctx *c, int f0, int nf, const uint8_t *left, const uint8_t *right,
+                                const float *lidar, bool cost, cudaStream_t s) {
+  const KParams &k = c->k;
+  const size_t px = (size_t)k.W * k.H;
+  const Buffers bp = frame_view(k, c->b, f0);
+  TIMED(c, "ingest", s, launch_ingest(k, bp, nf, left + f0 * px, right + f0 * px, lidar ? lidar + f0 * px : nullptr, s));
+  TIMED(c, "census", s, launch_census(k, bp, nf, f0, &c->mapL, &c->mapR, s));
+  if (k.semidense || need_boxc(k)) {
+    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end; the
+    // row-pass results of frames [f0, f0 + nf) in their own part of boxTmp
+    TIMED(c, "boxor", s, launch_boxor(k, nf, bp.dbar, c->b.boxTmp + (size_t)2 * f0 * k.MW * px,
+                                      k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s));
+  }
+  if (k.semidense) TIMED(c, "semidense", s, launch_semidense(k, bp, nf, s));
+  if (cost) TIMED(c, "cost", s, launch_cost(k, bp, nf, s));
+  return SGMF_OK;
+}
+
 extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *left, const uint8_t *right,
                                           const float *lidar, int16_t *out) {
   if (!c) return SGMF_ERR_ARG;
@@ -425,53 +522,52 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
     return fail(c, SGMF_ERR_ARG, "sgmf_compute_batch: need 1 <= n <= %d frames (got %d)", c->nb, n);
   if (c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute: a banded context needs sgmf_compute_banded");
   const KParams &k = c->k;
+  const size_t px = (size_t)k.W * k.H;
   cudaStream_t s = c->stream;
-  c->nrec = 0;
-  mark(c, "ingest");
-  LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
-  mark(c, "census");
-  LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
-  if (k.semidense || need_boxc(k)) {
-    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end
-    mark(c, "boxor");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.dbar, c->b.boxTmp, k.semidense ? c->b.boxS : nullptr,
-                               need_boxc(k) ? c->b.boxC : nullptr, s));
-  }
-  if (k.semidense) {
-    mark(c, "semidense");
-    LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
-  }
-  mark(c, "cost");
-  LAUNCH_TRY(c, launch_cost(k, c->b, n, s));
+  prof_reset(c);
   const KParams ka = agg_params(c);
   const int m = ka.sweep ? sweep_part(c, n) : 0;
-  mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
   if (m > 0) {
-    // part i: frames [i m, min(n, (i + 1) m)) through the sweep on the
-    // context's stream, then through the row kernel on the side stream
-    // while part i + 1 is in the sweep
-    for (int i = 0, f0 = 0; f0 < n; ++i, f0 += m) {
-      const int nf = std::min(m, n - f0);
+    // Parts of m frames.  Part i: its sweep on the context's stream, then
+    // its row kernel and check on the side stream, while part i + 1's
+    // front stages run on the front stream.  The side and front streams
+    // start after the work enqueued on the context's stream so far; the
+    // context's stream goes on after the last part's check.
+    const int parts = (n + m - 1) / m;
+    CUDA_TRY(c, cudaEventRecord(c->ev_in, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->front, c->ev_in, 0));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_in, 0));
+    sgmf_status st = front_stages(c, 0, std::min(m, n), left, right, lidar, true, c->front);
+    if (st != SGMF_OK) return st;
+    CUDA_TRY(c, cudaEventRecord(c->ev_front[0], c->front));
+    for (int i = 0; i < parts; ++i) {
+      const int f0 = i * m, nf = std::min(m, n - f0);
       const Buffers bp = frame_view(k, c->b, f0);
-      LAUNCH_TRY(c, launch_agg_sweep(ka, bp, nf, s));
+      CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_front[i], 0));
+      TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, bp, nf, s));
       CUDA_TRY(c, cudaEventRecord(c->ev_part[i], s));
+      if (i + 1 < parts) {
+        const int f1 = f0 + m;
+        st = front_stages(c, f1, std::min(m, n - f1), left, right, lidar, true, c->front);
+        if (st != SGMF_OK) return st;
+        CUDA_TRY(c, cudaEventRecord(c->ev_front[i + 1], c->front));
+      }
       CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part[i], 0));
-      LAUNCH_TRY(c, launch_agg_rows(ka, bp, nf, c->spill8, c->side));
+      TIMED(c, "agg_rows_wta", c->side, launch_agg_rows(ka, bp, nf, c->spill8, c->side));
+      TIMED(c, "consistency", c->side, launch_consistency(k, bp, nf, out + f0 * px, c->side));
     }
     CUDA_TRY(c, cudaEventRecord(c->ev_rows, c->side));
-    mark(c, "agg_rows_wta");
     CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_rows, 0));
   } else {
+    sgmf_status st = front_stages(c, 0, n, left, right, lidar, true, s);
+    if (st != SGMF_OK) return st;
     if (ka.sweep)
-      LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
+      TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, c->b, n, s));
     else
-      LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
-    mark(c, "agg_rows_wta");
-    LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
+      TIMED(c, "agg_lines", s, launch_agg_lines(ka, c->b, n, c->spill8, s));
+    TIMED(c, "agg_rows_wta", s, launch_agg_rows(ka, c->b, n, c->spill8, s));
+    TIMED(c, "consistency", s, launch_consistency(k, c->b, n, out, s));
   }
-  mark(c, "consistency");
-  LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
-  mark(c, "end");
   c->computed = true;
   c->last_n = n;
   return SGMF_OK;
@@ -507,10 +603,27 @@ static sgmf_status enqueue_host_batch(sgmf_ctx *c, int nf, const uint8_t *left, 
   const size_t cap = (size_t)c->k.W * c->k.H * c->nb;
   const size_t n = (size_t)c->k.W * c->k.H * nf;
   if (!c->st_left) {
-    CUDA_TRY(c, dalloc(c, &c->st_left, cap));
-    CUDA_TRY(c, dalloc(c, &c->st_right, cap));
-    CUDA_TRY(c, dalloc(c, &c->st_lidar, cap * 4));
-    CUDA_TRY(c, dalloc(c, &c->st_out, cap * 2));
+    // the four staging buffers, all or none
+    uint8_t *l = nullptr, *r = nullptr;
+    float *li = nullptr;
+    int16_t *o = nullptr;
+    const size_t held = c->bytes;
+    cudaError_t e = dalloc(c, &l, cap);
+    if (e == cudaSuccess) e = dalloc(c, &r, cap);
+    if (e == cudaSuccess) e = dalloc(c, &li, cap * 4);
+    if (e == cudaSuccess) e = dalloc(c, &o, cap * 2);
+    if (e != cudaSuccess) {
+      for (void *p : {(void *)l, (void *)r, (void *)li, (void *)o})
+        if (p) cudaFree(p);
+      c->bytes = held;
+      cudaGetLastError();
+      return fail(c, e == cudaErrorMemoryAllocation ? SGMF_ERR_OOM : SGMF_ERR_CUDA,
+                  "sgmf_compute_host: staging allocation failed: %s", cudaGetErrorString(e));
+    }
+    c->st_left = l;
+    c->st_right = r;
+    c->st_lidar = li;
+    c->st_out = o;
   }
   cudaStream_t s = c->stream;
   CUDA_TRY(c, cudaMemcpyAsync(c->st_left, left, n, cudaMemcpyHostToDevice, s));
@@ -626,18 +739,26 @@ extern "C" sgmf_status sgmf_set_profiling(sgmf_ctx *c, int enable) {
 
 extern "C" sgmf_status sgmf_kernel_times(sgmf_ctx *c, const char **names, float *ms, int *n) {
   if (!c || !n) return SGMF_ERR_ARG;
-  const int cap = *n;
-  int cnt = 0;
-  for (int i = 0; i + 1 < c->nrec; ++i) {
+  // the launches of each kernel name summed, names in order of first launch
+  std::vector<const char *> nm;
+  std::vector<float> tot;
+  for (const sgmf_ctx::ProfRec &r : c->recs) {
     float t = 0.f;
-    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
-    if (cnt < cap) {
-      if (names) names[cnt] = c->names[i];
-      if (ms) ms[cnt] = t;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, r.a, r.b));
+    size_t j = 0;
+    while (j < nm.size() && strcmp(nm[j], r.name) != 0) ++j;
+    if (j == nm.size()) {
+      nm.push_back(r.name);
+      tot.push_back(0.f);
     }
-    ++cnt;
+    tot[j] += t;
   }
-  *n = cnt;
+  const int cap = *n;
+  for (int i = 0; i < (int)nm.size() && i < cap; ++i) {
+    if (names) names[i] = nm[i];
+    if (ms) ms[i] = tot[i];
+  }
+  *n = (int)nm.size();
   return SGMF_OK;
 }
 
@@ -747,25 +868,10 @@ extern "C" sgmf_status sgmf_compute_front(sgmf_ctx *c, int n, const uint8_t *lef
   if (!c->k.band) return fail(c, SGMF_ERR_ARG, "sgmf_compute_front: context is not banded (sgmf_create_banded)");
   if (n < 1 || n > c->nb)
     return fail(c, SGMF_ERR_ARG, "sgmf_compute_front: need 1 <= n <= %d frames (got %d)", c->nb, n);
-  const KParams &k = c->k;
-  cudaStream_t s = c->stream;
-  c->nrec = 0;
-  mark(c, "ingest");
-  LAUNCH_TRY(c, launch_ingest(k, c->b, n, left, right, lidar, s));
-  mark(c, "census");
-  LAUNCH_TRY(c, launch_census(k, c->b, n, &c->mapL, &c->mapR, s));
-  if (k.semidense || need_boxc(k)) {
-    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end
-    mark(c, "boxor");
-    LAUNCH_TRY(c, launch_boxor(k, n, c->b.dbar, c->b.boxTmp, k.semidense ? c->b.boxS : nullptr,
-                               need_boxc(k) ? c->b.boxC : nullptr, s));
-  }
-  if (k.semidense) {
-    mark(c, "semidense");
-    LAUNCH_TRY(c, launch_semidense(k, c->b, n, s));
-  }
-  mark(c, "between_halves");   // the caller's band proposal runs until the back half starts
-  c->front_n = n;
+  prof_reset(c);
+  const sgmf_status st = front_stages(c, 0, n, left, right, lidar, false, c->stream);
+  if (st != SGMF_OK) return st;
+  c->front_n = n;   // the caller's band proposal runs before the back half
   return SGMF_OK;
 }
 
@@ -784,20 +890,15 @@ extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_
   if (c->k.subpixel) return fail(c, SGMF_ERR_PARAM, "sgmf_compute_banded: subpixel must be 0");
   const KParams &k = c->k;
   cudaStream_t s = c->stream;
-  LAUNCH_TRY(c, launch_band_clamp(k, c->b, n, band_lo, s));
-  mark(c, "cost");
-  LAUNCH_TRY(c, launch_cost_banded(k, c->b, n, s));
+  TIMED(c, "band_clamp", s, launch_band_clamp(k, c->b, n, band_lo, s));
+  TIMED(c, "cost", s, launch_cost_banded(k, c->b, n, s));
   const KParams ka = agg_params(c);
-  mark(c, ka.sweep ? "agg_sweep" : "agg_lines");
   if (ka.sweep)
-    LAUNCH_TRY(c, launch_agg_sweep(ka, c->b, n, s));
+    TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, c->b, n, s));
   else
-    LAUNCH_TRY(c, launch_agg_lines(ka, c->b, n, c->spill8, s));
-  mark(c, "agg_rows_wta");
-  LAUNCH_TRY(c, launch_agg_rows(ka, c->b, n, c->spill8, s));
-  mark(c, "consistency");
-  LAUNCH_TRY(c, launch_consistency(k, c->b, n, out, s));
-  mark(c, "end");
+    TIMED(c, "agg_lines", s, launch_agg_lines(ka, c->b, n, c->spill8, s));
+  TIMED(c, "agg_rows_wta", s, launch_agg_rows(ka, c->b, n, c->spill8, s));
+  TIMED(c, "consistency", s, launch_consistency(k, c->b, n, out, s));
   c->computed = true;
   c->last_n = n;
   c->front_n = 0;

@@ -643,9 +643,8 @@ extern "C" sgmf_status sgmf_bn_conv(int n, int h, int w, const uint16_t *x, cons
   const long long ntile = (long long)n * h * ((w + kCvM - 1) / kCvM);
   // one wave of about four CTAs per SM, each walking consecutive tiles with
   // its weights staged once
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0;
+  const cudaError_t e = sm_count(&sms);
   if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_conv");
   const long long slots = 4LL * std::max(sms, 1);
   const int tiles = (int)std::max<long long>(1, std::min<long long>(32, (ntile + slots - 1) / slots));
@@ -670,13 +669,10 @@ extern "C" sgmf_status sgmf_bn_wgrad(int n, int h, int w, const uint16_t *x, con
                                      int *err, void *stream) {
   if (n < 1 || h < 1 || w < 1 || !x || !dy || !dw || !db || !err) return SGMF_ERR_ARG;
   static bool attr[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_bn_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
-    if (e != cudaSuccess) return bn_launch(e, "sgmf_bn_wgrad attribute");
-    attr[dev] = true;
-  }
+  const cudaError_t ea = once_per_device(attr, [](int) {
+    return cudaFuncSetAttribute(k_bn_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+  });
+  if (ea != cudaSuccess) return bn_launch(ea, "sgmf_bn_wgrad attribute");
   const long long P = (long long)n * h * w;
   const long long nchunk = (P + 127) / 128;
   const int chunks = (int)((nchunk + kWgMaxCtas - 1) / kWgMaxCtas);

@@ -99,8 +99,11 @@ __device__ __forceinline__ uint64_t census_bits(const uint8_t (*T)[kCenBoxW], in
   return c;
 }
 
+// b0 holds the buffers of the launch's first frame, which is frame zoff of
+// the tensor maps (their third coordinate)
 template <bool FULL>
-__global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __grid_constant__ CUtensorMap mapL,
+__global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, int zoff,
+                                                const __grid_constant__ CUtensorMap mapL,
                                                 const __grid_constant__ CUtensorMap mapR) {
   const int f = blockIdx.z;
   const Buffers b = frame_view(k, b0, f);
@@ -116,12 +119,12 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __g
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, 2u * kCenBoxW * kCenBoxH);
-    tma_load_3d(tiles, &mapL, x0 - 16, y0 - 3, f, &bar);
-    tma_load_3d(tiles + kBoxBytes, &mapR, x0 - 16, y0 - 3, f, &bar);
+    tma_load_3d(tiles, &mapL, x0 - 16, y0 - 3, zoff + f, &bar);
+    tma_load_3d(tiles + kBoxBytes, &mapR, x0 - 16, y0 - 3, zoff + f, &bar);
   }
-  if (!mbar_wait_bounded(&bar, 0, kWaitLimit)) {
+  if (!mbar_wait_bounded(&bar, 0, k.wait_census)) {
     set_error(b.err, kErrTimeout);
-    mbar_wait_bounded(&bar, 0, kWaitLimit);   // give the copies in flight a second chance
+    mbar_wait_bounded(&bar, 0, kWaitLimit);   // the copies in flight land before the CTA exits
     return;
   }
   const bool interior = x0 >= 4 && x0 + kCenTileW + 4 <= k.W && y0 >= 3 && y0 + kCenTileH + 3 <= k.H;
@@ -145,15 +148,15 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, const __g
   }
 }
 
-cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
+cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, int zoff, const void *tmaL, const void *tmaR,
                           cudaStream_t s) {
   dim3 grid((k.W + kCenTileW - 1) / kCenTileW, (k.H + kCenTileH - 1) / kCenTileH, nf);
   const CUtensorMap &mL = *static_cast<const CUtensorMap *>(tmaL);
   const CUtensorMap &mR = *static_cast<const CUtensorMap *>(tmaR);
   if (k.census == 1)
-    k_census<true><<<grid, 256, 0, s>>>(k, b, mL, mR);
+    k_census<true><<<grid, 256, 0, s>>>(k, b, zoff, mL, mR);
   else
-    k_census<false><<<grid, 256, 0, s>>>(k, b, mL, mR);
+    k_census<false><<<grid, 256, 0, s>>>(k, b, zoff, mL, mR);
   return cudaGetLastError();
 }
 
@@ -354,21 +357,17 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static bool done[64] = {};
-  static int sms[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!done[dev]) {
-    e = cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    done[dev] = true;
-  }
+  e = once_per_device(done, [](int) {
+    return cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
+  });
+  int sms = 0;
+  if (e == cudaSuccess) e = sm_count(&sms);
+  if (e != cudaSuccess) return e;
   // the longest segment whose grid still makes about two waves of one-warp
   // CTAs (about 20 resident a SM at r = 20)
   const long ctas_per_seg = (long)((k.W + 31) / 32) * 2 * nf * k.MW;
   int seg = kColSeg;
-  while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms[dev]) seg /= 2;
+  while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms) seg /= 2;
   // y: row segment x radius (bit 0), z: frame x word plane
   dim3 g((k.W + 31) / 32, 2 * ((k.H + seg - 1) / seg), nf * k.MW);
   k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc, seg);

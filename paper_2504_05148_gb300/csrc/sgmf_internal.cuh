@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -44,7 +45,8 @@ struct KParams {
   int sweep_cs;               // CTAs per sweep cluster (0: the sweep cannot run this context)
   int parts;                  // tuning: 1 = sweep batches in parts (row kernels on a second stream)
   int band;                   // banded mode: band width B (= Dp); 0 = the plain method
-  int tw, th;                 // banded mode: band tiles per row / column                  // census bits (31 or 62)
+  int tw, th;                 // banded mode: band tiles per row / column
+  uint32_t wait_census;       // poll limit of the census kernel's TMA wait (kWaitLimit by default)
 };
 
 struct Buffers {   // base pointers of frame 0
@@ -193,6 +195,29 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// ---- per-device one-time set-up (host) --------------------------------------
+// Kernel attributes and device properties are set or read once per device
+// ordinal.  The library's entry points may be called from any host thread,
+// so the flags are read and written under one process-wide mutex.
+std::mutex &setup_mutex();
+
+// runs setup(dev) once for the current device; cudaSuccess afterwards
+template <typename F>
+inline cudaError_t once_per_device(bool (&done)[64], F &&setup) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(setup_mutex());
+  if (done[dev]) return cudaSuccess;
+  e = setup(dev);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+// number of SMs of the current device (looked up once per device)
+cudaError_t sm_count(int *out);
+
 // ---- kernel launchers (implemented in the .cu files) -----------------------
 struct TmaMaps;   // opaque holder of the two image tensor maps (sgmf_front.cu)
 
@@ -217,7 +242,8 @@ inline CostTable cost_table(const KParams &k) {
 
 cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint8_t *left,
                           const uint8_t *right, const float *lidar, cudaStream_t s);
-cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, const void *tmaL, const void *tmaR,
+// b: the buffers of frame zoff (frame_view), which is the tensor maps' frame zoff
+cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, int zoff, const void *tmaL, const void *tmaR,
                           cudaStream_t s);
 // box-ORs of the presence masks of the sparse map disp [nf][H][W] (values in
 // [0, D) present): radius k.rs into boxS and k.rc into boxC, either may be

@@ -13,6 +13,7 @@
 // The array is shared by every call: calls that overlap on the GPU (other
 // streams, other host threads) race on it.  Every word a call reads is
 // written earlier in the same call, so nothing carries over between calls.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -51,26 +52,60 @@ __global__ void __launch_bounds__(256) k_static_dbar(int W, int H, int D, const 
 
 namespace {
 std::mutex g_addr_mu;
-uint32_t *g_addr[64] = {};   // device address of g_check_scratch per device ordinal
+uint32_t *g_addr[64] = {};            // device address of g_check_scratch per device ordinal
+unsigned long long g_ctx_id[64] = {}; // the context that address belongs to
 
 sgmf_status fail_static(sgmf_status s, const std::string &msg) {
   set_noctx_error(msg);
   return s;
 }
 
-// device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached
+// Unique id of the calling thread's current CUDA context, 0 when there is
+// none or it is no longer valid (driver entry points, so that the library
+// needs no link against the driver library).
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext *);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {   // under g_addr_mu
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(p);
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up
+// with that device current and cached per device.  The cache belongs to the
+// context it was read in: when the current context is another one (the
+// device was reset with cudaDeviceReset and its primary context made anew),
+// the address is looked up again.
 cudaError_t scratch_address(uint32_t **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (g_addr[dev] == nullptr) {
+  const unsigned long long id = g_addr[dev] != nullptr ? current_context_id() : 0;
+  if (g_addr[dev] == nullptr || id == 0 || id != g_ctx_id[dev]) {
     void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_check_scratch);
+    e = cudaGetSymbolAddress(&ptr, g_check_scratch);   // makes the device's context current if needed
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<uint32_t *>(ptr);
+    g_ctx_id[dev] = current_context_id();
   }
   *out = g_addr[dev];
   return cudaSuccess;

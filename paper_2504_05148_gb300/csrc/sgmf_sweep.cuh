@@ -32,6 +32,8 @@
 // barriers, at the start and the end, are executed by every thread.
 #pragma once
 
+#include <type_traits>
+
 #include "sgmf_aggregate.cuh"
 
 namespace sgmf {
@@ -63,10 +65,11 @@ struct SweepCfg {
   // at least kExclusive bytes: one CTA per SM, so that the clusters the
   // device holds at once are the SMs the sweep occupies
   static constexpr int kExclusive = 120 * 1024;
-  // ring, barriers, exchange slots, one band-shift buffer (Dp u16) per group
+  // ring, barriers, exchange slots, one band-shift buffer (Dp u16) and the
+  // edge words of its 3P + 2 vectors (two words each) per group
   static constexpr int smem_bytes(int warps) {
     return max(kExclusive, R * (2 * warps * P) * Dp + (R + 5) * 8 + 2 * 2 * (2 * warps) * kSlot * 4 +
-                               (2 * warps) * Dp * 2);
+                               (2 * warps) * Dp * 2 + (2 * warps) * (3 * P + 2) * 2 * 4);
   }
 };
 
@@ -115,6 +118,16 @@ __device__ __forceinline__ void sweep_step(uint32_t (&out)[NW], uint32_t &mout, 
                                            uint32_t edge_lo, uint32_t edge_hi, int grp) {
   copy_vec<NW>(out, pred);
   sgm_step<NW>(out, C, mpred, sc, edge_lo, edge_hi);
+  mout = group_min<NW>(out, grp);
+}
+
+// the same on the bands, with the predecessor's edge word e (sgm_step_e)
+template <int NW>
+__device__ __forceinline__ void sweep_step_e(uint32_t (&out)[NW], uint32_t &mout, const uint32_t (&pred)[NW],
+                                             uint32_t mpred, const uint32_t (&C)[NW], const StepConsts &sc,
+                                             uint32_t e, int lig, int grp) {
+  copy_vec<NW>(out, pred);
+  sgm_step_e<NW>(out, C, mpred, sc, e, lig);
   mout = group_min<NW>(out, grp);
 }
 
@@ -214,6 +227,15 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
   const uint32_t keep_in_l = xg == 0 ? 0u : 0xffffffffu;
   // warps whose groups touch neither border need none of the masks below
   const bool plain = __all_sync(kFull, xg > 0 && xg + P < W);
+  // one Eq. 2 step from a predecessor vector; on the bands with the
+  // predecessor's edge word (all ones but on the first step after a shift)
+  auto step = [&](uint32_t(&o)[NW], uint32_t &mo, const uint32_t(&pr)[NW], uint32_t mp, const uint32_t(&Cc)[NW],
+                  uint32_t e) {
+    if constexpr (BANDED)
+      sweep_step_e<NW>(o, mo, pr, mp, Cc, sc, e, lig, grp);
+    else
+      sweep_step<NW>(o, mo, pr, mp, Cc, sc, edge_lo, edge_hi, grp);
+  };
   bool ok = true;
   auto bounded = [&](uint64_t *bar, uint32_t parity) {
     if (!mbar_wait_bounded(bar, parity, kWaitLimit)) {
@@ -222,166 +244,204 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
     }
   };
 
+  // banded: the edge words of the group's vectors on a row that re-indexes
+  // them (sgm_step_e), [vector][lane 0 / lane 15]: V[i] = i, DL[i] = P + i,
+  // DR[i] = 2P + i, the vector entering from the left 3P, from the right 3P + 1
+  constexpr int NE = 3 * P + 2;
+  uint32_t *esm = reinterpret_cast<uint32_t *>(reinterpret_cast<uint16_t *>(slots + 2 * 2 * ng * SL) + ng * Dp) +
+                  gi * NE * 2 + (lig == 15 ? 1 : 0);
+  // re-index a vector to this row's band and record its edge word (lanes 0 and 15)
+  auto shift_rec = [&](uint32_t(&v)[NW], int delta, int k) {
+    uint32_t e = 0xffffffffu;
+    band_shift<CPL>(v, delta, shbuf, lig, e);
+    if (lig == 0 || lig == 15) esm[2 * k] = e;
+  };
+
   for (int t = 0; t < H; ++t) {
     bounded(&bars[t % R], (uint32_t)(t / R) & 1u);
     const uint8_t *st = ring + (size_t)(t % R) * strip * Dp + gi * P * Dp + lig * CPL;
     const int y = up ? H - 1 - t : t, yp = up ? y + 1 : y - 1;   // this row, the previous one
-    int lo_cur = 0;
+    int delta = 0, dl = 0, dr = 0;
+    bool shifted = false;
     if constexpr (BANDED) {
-      // a new band tile row: every vector of the group moves to the new band
-      // (cells without a counterpart in the old band become absent)
-      lo_cur = lo_at(xg, y);
+      // the band change of the group's own vectors (a new band tile row) and
+      // of the vectors entering from the neighbours (pixel x - 1 or x + P of
+      // the previous row, in their own bands)
+      const int lo_cur = lo_at(xg, y);
       if (t > 0) {
-        const int delta = lo_cur - lo_at(xg, yp);
+        delta = lo_cur - lo_at(xg, yp);
+        dl = lo_cur - lo_at(xg - 1, yp);
+        dr = lo_cur - lo_at(xg + P, yp);
+      }
+      shifted = __any_sync(kFull, delta != 0 || dl != 0 || dr != 0);
+      if (shifted) {
+        if (lig == 0 || lig == 15) {
+#pragma unroll
+          for (int k = 0; k < NE; ++k) esm[2 * k] = 0xffffffffu;
+        }
+        // every vector of the group moves to the new band (cells without a
+        // counterpart in the old band become absent; the old cell just
+        // outside the new band goes to the edge word)
         if (__any_sync(kFull, delta != 0)) {
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            band_shift<CPL>(V[i], delta, shbuf, lig);
-            band_shift<CPL>(DL[i], delta, shbuf, lig);
-            band_shift<CPL>(DR[i], delta, shbuf, lig);
+            shift_rec(V[i], delta, i);
+            shift_rec(DL[i], delta, P + i);
+            shift_rec(DR[i], delta, 2 * P + i);
           }
         }
       }
     }
-    uint32_t C0[NW], CP[NW];
-    unpack_u8<CPL>(st, z, C0);
-    unpack_u8<CPL>(st + (P - 1) * Dp, z, CP);
-    // the two vectors this group sends: from-left of its last pixel (from
-    // its own pixel P-2), from-right of its first pixel (from its pixel 1)
-    uint32_t eL[NW], eR[NW], meL, meR;
-    {
-      uint32_t pr[NW], mpr = mR[1];
-      copy_vec<NW>(pr, DR[1]);
-      if (!plain) {
-        const uint32_t kr = xg + 1 < W ? 0xffffffffu : 0u;   // pixel 0's right predecessor inside
-#pragma unroll
-        for (int w = 0; w < NW; ++w) pr[w] &= kr;
-        mpr &= kr;
-      }
-      sweep_step<NW>(eL, meL, DL[P - 2], mL[P - 2], CP, sc, edge_lo, edge_hi, grp);
-      sweep_step<NW>(eR, meR, pr, mpr, C0, sc, edge_lo, edge_hi, grp);
-    }
-    // the vectors entering this group from the previous row
-    uint32_t inL[NW], inR[NW], minL = 0u, minR = 0u;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) inL[w] = inR[w] = 0u;
-    if (t > 0) {
-      const int par = (t - 1) & 1;
-      // every warp of the CTA has stored row t - 1's vectors (and finished row t - 2)
-      bounded(rowbar, (uint32_t)(t - 1) & 1u);
-      if (recv_l || recv_r) {
-        uint64_t *mb = &rx[(recv_l ? 0 : 1) * 2 + par];
-        if (lig == 0) mbar_expect_tx(mb, kMsgBytes);
-        bounded(mb, (uint32_t)((t - 1) >> 1) & 1u);
-      }
-      const uint32_t *sl = slot(0, par, gi), *sr = slot(1, par, gi);
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        inL[w] = sl[w * 16];
-        inR[w] = sr[w * 16];
-      }
-      minL = sl[NW * 16];
-      minR = sr[NW * 16];
-      if constexpr (BANDED) {
-        // the neighbours' vectors are in their own bands (pixel x - 1 or
-        // x + P of the previous row)
-        const int dl = lo_cur - lo_at(xg - 1, yp), dr = lo_cur - lo_at(xg + P, yp);
-        if (__any_sync(kFull, dl != 0)) band_shift<CPL>(inL, dl, shbuf, lig);
-        if (__any_sync(kFull, dr != 0)) band_shift<CPL>(inR, dr, shbuf, lig);
-      }
-    }
-    // the ring stage of row t - 2 is free: every warp finished that row before its row t - 1 arrival
-    if (threadIdx.x == 0 && issued < H && issued <= t + 2) issue(issued);
-    if (t + 1 < H) {
-      // row t's outgoing vectors (the last row's have no reader)
-      const int par = t & 1;
-      if (send_r) {
-        if (remote_r) {
-          const uint32_t dst = par ? dst_r1 : dst_r0, mb = par ? mb_r1 : mb_r0;
-#pragma unroll
-          for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eL[w], mb);
-          st_async(dst + NW * 64, meL, mb);
-        } else {
-          uint32_t *d = slot(0, par, g_r);
-#pragma unroll
-          for (int w = 0; w < NW; ++w) d[w * 16] = eL[w];
-          d[NW * 16] = meL;
-        }
-      }
-      if (send_l) {
-        if (remote_l) {
-          const uint32_t dst = par ? dst_l1 : dst_l0, mb = par ? mb_l1 : mb_l0;
-#pragma unroll
-          for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eR[w], mb);
-          st_async(dst + NW * 64, meR, mb);
-        } else {
-          uint32_t *d = slot(1, par, g_l);
-#pragma unroll
-          for (int w = 0; w < NW; ++w) d[w * 16] = eR[w];
-          d[NW * 16] = meR;
-        }
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(rowbar);
-    // the rest of the row
-    if (!plain) {
-      const uint32_t kl = keep_in_l, kr = xg + P < W ? 0xffffffffu : 0u;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        inL[w] &= kl;
-        inR[w] &= kr;
-      }
-      minL &= kl;
-      minR &= kr;
-    }
-    uint32_t carry[NW], mcarry = mL[0];
-    copy_vec<NW>(carry, DL[0]);
-    sweep_step<NW>(DL[0], mL[0], inL, minL, C0, sc, edge_lo, edge_hi, grp);
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      uint32_t C[NW];
-      if (i == 0)
-        copy_vec<NW>(C, C0);
-      else if (i == P - 1)
-        copy_vec<NW>(C, CP);
-      else
-        unpack_u8<CPL>(st + i * Dp, z, C);
-      uint32_t mtmp;
-      sweep_step<NW>(V[i], mtmp, V[i], mV[i], C, sc, edge_lo, edge_hi, grp);
-      mV[i] = mtmp;
-      if (i >= 1 && i <= P - 2) {
-        uint32_t nxt[NW];
-        const uint32_t mnxt = mL[i];
-        copy_vec<NW>(nxt, DL[i]);
-        sweep_step<NW>(DL[i], mL[i], carry, mcarry, C, sc, edge_lo, edge_hi, grp);
-        copy_vec<NW>(carry, nxt);
-        mcarry = mnxt;
-        uint32_t pr[NW], mpr = mR[i + 1];
-        copy_vec<NW>(pr, DR[i + 1]);
+    // the row's work; E: with the edge words of a re-indexing row
+    auto row = [&](auto edges) {
+      constexpr bool E = decltype(edges)::value;
+      auto edge = [&](int k) -> uint32_t {
+        if constexpr (E)
+          return esm[2 * k];
+        else
+          return 0xffffffffu;
+      };
+      uint32_t C0[NW], CP[NW];
+      unpack_u8<CPL>(st, z, C0);
+      unpack_u8<CPL>(st + (P - 1) * Dp, z, CP);
+      // the two vectors this group sends: from-left of its last pixel (from
+      // its own pixel P-2), from-right of its first pixel (from its pixel 1)
+      uint32_t eL[NW], eR[NW], meL, meR;
+      {
+        uint32_t pr[NW], mpr = mR[1];
+        copy_vec<NW>(pr, DR[1]);
         if (!plain) {
-          const uint32_t ki = xg + i + 1 < W ? 0xffffffffu : 0u;
+          const uint32_t kr = xg + 1 < W ? 0xffffffffu : 0u;   // pixel 0's right predecessor inside
 #pragma unroll
-          for (int w = 0; w < NW; ++w) pr[w] &= ki;
-          mpr &= ki;
+          for (int w = 0; w < NW; ++w) pr[w] &= kr;
+          mpr &= kr;
         }
-        sweep_step<NW>(DR[i], mR[i], pr, mpr, C, sc, edge_lo, edge_hi, grp);
-      } else if (i == 0) {
-        copy_vec<NW>(DR[0], eR);
-        mR[0] = meR;
-      } else {
-        copy_vec<NW>(DL[P - 1], eL);
-        mL[P - 1] = meL;
-        sweep_step<NW>(DR[P - 1], mR[P - 1], inR, minR, C, sc, edge_lo, edge_hi, grp);
+        step(eL, meL, DL[P - 2], mL[P - 2], CP, edge(2 * P - 2));
+        step(eR, meR, pr, mpr, C0, edge(2 * P + 1));
       }
-      const int x = xg + i;
-      if (ok && x < W) {
-        uint32_t s[NW];
+      // the vectors entering this group from the previous row
+      uint32_t inL[NW], inR[NW], minL = 0u, minR = 0u;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s[w] = V[i][w] + DL[i][w] + DR[i][w];
-        store_u16<CPL>(out + ((size_t)y * W + x) * Dp, s);
+      for (int w = 0; w < NW; ++w) inL[w] = inR[w] = 0u;
+      if (t > 0) {
+        const int par = (t - 1) & 1;
+        // every warp of the CTA has stored row t - 1's vectors (and finished row t - 2)
+        bounded(rowbar, (uint32_t)(t - 1) & 1u);
+        if (recv_l || recv_r) {
+          uint64_t *mb = &rx[(recv_l ? 0 : 1) * 2 + par];
+          if (lig == 0) mbar_expect_tx(mb, kMsgBytes);
+          bounded(mb, (uint32_t)((t - 1) >> 1) & 1u);
+        }
+        const uint32_t *sl = slot(0, par, gi), *sr = slot(1, par, gi);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          inL[w] = sl[w * 16];
+          inR[w] = sr[w * 16];
+        }
+        minL = sl[NW * 16];
+        minR = sr[NW * 16];
+        if constexpr (E) {
+          if (__any_sync(kFull, dl != 0)) shift_rec(inL, dl, 3 * P);
+          if (__any_sync(kFull, dr != 0)) shift_rec(inR, dr, 3 * P + 1);
+        }
       }
-    }
+      // the ring stage of row t - 2 is free: every warp finished that row before its row t - 1 arrival
+      if (threadIdx.x == 0 && issued < H && issued <= t + 2) issue(issued);
+      if (t + 1 < H) {
+        // row t's outgoing vectors (the last row's have no reader)
+        const int par = t & 1;
+        if (send_r) {
+          if (remote_r) {
+            const uint32_t dst = par ? dst_r1 : dst_r0, mb = par ? mb_r1 : mb_r0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eL[w], mb);
+            st_async(dst + NW * 64, meL, mb);
+          } else {
+            uint32_t *d = slot(0, par, g_r);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) d[w * 16] = eL[w];
+            d[NW * 16] = meL;
+          }
+        }
+        if (send_l) {
+          if (remote_l) {
+            const uint32_t dst = par ? dst_l1 : dst_l0, mb = par ? mb_l1 : mb_l0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) st_async(dst + w * 64, eR[w], mb);
+            st_async(dst + NW * 64, meR, mb);
+          } else {
+            uint32_t *d = slot(1, par, g_l);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) d[w * 16] = eR[w];
+            d[NW * 16] = meR;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(rowbar);
+      // the rest of the row
+      if (!plain) {
+        const uint32_t kl = keep_in_l, kr = xg + P < W ? 0xffffffffu : 0u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          inL[w] &= kl;
+          inR[w] &= kr;
+        }
+        minL &= kl;
+        minR &= kr;
+      }
+      uint32_t carry[NW], mcarry = mL[0];
+      copy_vec<NW>(carry, DL[0]);
+      step(DL[0], mL[0], inL, minL, C0, edge(3 * P));
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        uint32_t C[NW];
+        if (i == 0)
+          copy_vec<NW>(C, C0);
+        else if (i == P - 1)
+          copy_vec<NW>(C, CP);
+        else
+          unpack_u8<CPL>(st + i * Dp, z, C);
+        uint32_t mtmp;
+        step(V[i], mtmp, V[i], mV[i], C, edge(i));
+        mV[i] = mtmp;
+        if (i >= 1 && i <= P - 2) {
+          uint32_t nxt[NW];
+          const uint32_t mnxt = mL[i];
+          copy_vec<NW>(nxt, DL[i]);
+          step(DL[i], mL[i], carry, mcarry, C, edge(P + i - 1));
+          copy_vec<NW>(carry, nxt);
+          mcarry = mnxt;
+          uint32_t pr[NW], mpr = mR[i + 1];
+          copy_vec<NW>(pr, DR[i + 1]);
+          if (!plain) {
+            const uint32_t ki = xg + i + 1 < W ? 0xffffffffu : 0u;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) pr[w] &= ki;
+            mpr &= ki;
+          }
+          step(DR[i], mR[i], pr, mpr, C, edge(2 * P + i + 1));
+        } else if (i == 0) {
+          copy_vec<NW>(DR[0], eR);
+          mR[0] = meR;
+        } else {
+          copy_vec<NW>(DL[P - 1], eL);
+          mL[P - 1] = meL;
+          step(DR[P - 1], mR[P - 1], inR, minR, C, edge(3 * P + 1));
+        }
+        const int x = xg + i;
+        if (ok && x < W) {
+          uint32_t sum[NW];
+#pragma unroll
+          for (int w = 0; w < NW; ++w) sum[w] = V[i][w] + DL[i][w] + DR[i][w];
+          store_u16<CPL>(out + ((size_t)y * W + x) * Dp, sum);
+        }
+      }
+    };
+    if (BANDED && shifted)
+      row(std::true_type{});
+    else
+      row(std::false_type{});
   }
   // every message was waited for by its receiver; the cluster barrier keeps
   // every CTA (and its shared memory) alive until all are done
@@ -425,15 +485,13 @@ static cudaLaunchConfig_t sweep_config(int nf, int ctas, int warps, cudaStream_t
 template <int CPL, bool BANDED>
 static cudaError_t sweep_attributes() {
   static bool done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SweepCfg<CPL, BANDED>::smem_bytes(SweepCfg<CPL, BANDED>::kMaxWarps));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
-  return e;
+  return once_per_device(done, [](int) {
+    cudaError_t e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SweepCfg<CPL, BANDED>::smem_bytes(SweepCfg<CPL, BANDED>::kMaxWarps));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_agg_sweep<CPL, BANDED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+  });
 }
 
 // The cluster size (CTAs per cluster) for the sweep of a context that runs

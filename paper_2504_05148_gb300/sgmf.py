@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsgmf.so")
 SGMF_OK, SGMF_ERR_ARG, SGMF_ERR_PARAM, SGMF_ERR_SHAPE, SGMF_ERR_OOM, SGMF_ERR_CUDA, SGMF_ERR_TIMEOUT = range(7)
 SGMF_CENSUS_CS9X7, SGMF_CENSUS_9X7 = 0, 1
 SGMF_CHECK_STEREO_LIDAR, SGMF_CHECK_STEREO, SGMF_CHECK_LIDAR, SGMF_CHECK_NONE = 0, 1, 2, 3
+SGMF_WAIT_CENSUS = 0
 BAND_TILE = 8   # banded mode: pixels per side of a band tile (include/sgmf.h)
 (SGMF_STAGE_DBAR, SGMF_STAGE_CENSUS_L, SGMF_STAGE_CENSUS_R, SGMF_STAGE_DHAT, SGMF_STAGE_COST,
  SGMF_STAGE_SUM, SGMF_STAGE_DSTAR, SGMF_STAGE_DPRIME, SGMF_STAGE_DSUB, SGMF_STAGE_BOX_S,
@@ -32,6 +33,7 @@ EXPORTS = (
     "sgmf_compute_host_batch", "sgmf_sync", "sgmf_destroy", "sgmf_last_error",
     "sgmf_status_string", "sgmf_set_debug", "sgmf_debug_stage", "sgmf_launches_per_compute",
     "sgmf_set_profiling", "sgmf_kernel_times", "sgmf_device_bytes", "sgmf_check_static",
+    "sgmf_set_wait_limit", "sgmf_debug_fail_alloc", "sgmf_measure_rates",
     "sgmf_set_tuning", "sgmf_get_tuning", "sgmf_autotune",
     "sgmf_multi_create", "sgmf_multi_frame", "sgmf_multi_classes", "sgmf_multi_class_info",
     "sgmf_multi_autotune", "sgmf_multi_launch", "sgmf_multi_sync", "sgmf_multi_launches",
@@ -55,6 +57,11 @@ class sgmf_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "p1", "p2", "q1", "q2", "alpha_num", "alpha_den", "ts", "rs", "tc", "rc",
         "lr_max_diff", "census", "semidense", "consistency", "num_paths", "subpixel")]
+
+
+class sgmf_rates(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int)] + [(k, ctypes.c_double) for k in (
+        "min3_u16x2", "addmin_u16x2", "iadd", "popc", "prmt")]
 
 
 class sgmf_tuning(ctypes.Structure):
@@ -148,6 +155,9 @@ def lib(path: str | None = None):
         "sgmf_kernel_times": (i, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_int)]),
         "sgmf_device_bytes": (sz, [P]),
+        "sgmf_set_wait_limit": (i, [P, i, ctypes.c_longlong]),
+        "sgmf_debug_fail_alloc": (None, [i]),
+        "sgmf_measure_rates": (i, [i, ctypes.POINTER(sgmf_rates)]),
         "sgmf_check_static": (i, [i, i, i, prm_p, P, P, P, P, P]),
         "sgmf_set_tuning": (i, [P, ctypes.POINTER(sgmf_tuning)]),
         "sgmf_get_tuning": (i, [P, ctypes.POINTER(sgmf_tuning)]),
@@ -308,6 +318,23 @@ def sgmf_kernel_times(ctx: int, cap: int = 32) -> list[tuple[str, float]]:
 
 def sgmf_device_bytes(ctx: int) -> int:
     return lib().sgmf_device_bytes(ctx)
+
+
+def sgmf_set_wait_limit(ctx: int, which: int, polls: int) -> None:
+    """Poll limit of one kind of device wait (polls < 0: the default)."""
+    _check(lib().sgmf_set_wait_limit(ctx, which, polls), ctx)
+
+
+def sgmf_debug_fail_alloc(n: int) -> None:
+    """Test hook: the n-th device allocation from now on, on this thread, fails (n <= 0: off)."""
+    lib().sgmf_debug_fail_alloc(n)
+
+
+def sgmf_measure_rates(iters: int = 256) -> dict:
+    """Lanes per clock per SM of the path's instruction kinds on the current device."""
+    r = sgmf_rates()
+    _check(lib().sgmf_measure_rates(iters, ctypes.byref(r)), None)
+    return {k: getattr(r, k) for k, _ in sgmf_rates._fields_}
 
 
 def sgmf_check_static(width: int, height: int, max_disp: int, params: Params, dstar: int, dprime: int,

@@ -77,6 +77,16 @@ def test_tuning_and_shape_structs_match_header():
     assert [f[0] for f in sgmf.sgmf_shape._fields_] == _int32_fields("sgmf_shape")
 
 
+def test_rates_struct_matches_header():
+    """sgmf_rates: one int (sms), then doubles in the header's order."""
+    h = open(os.path.join(ROOT, "include", "sgmf.h")).read()
+    body = h[h.index("typedef struct {\n  int sms;"):]
+    body = body[:body.index("} sgmf_rates;")]
+    names = [ln.split(";")[0].split()[-1] for ln in body.splitlines()[1:] if ";" in ln]
+    assert [f[0] for f in sgmf.sgmf_rates._fields_] == names
+    assert sgmf.sgmf_rates._fields_[0][1] is ctypes.c_int
+
+
 def test_status_strings(libpath):
     assert sgmf.lib().sgmf_status_string(sgmf.SGMF_ERR_PARAM) == b"SGMF_ERR_PARAM"
     assert sgmf.lib().sgmf_status_string(sgmf.SGMF_OK) == b"SGMF_OK"

@@ -34,7 +34,21 @@ def _pipeline(scene, params):
         ctx.close()
 
 
-def _static(scene, params, dstar, dprime):
+def _pipeline_nolidar(scene, params):
+    """As _pipeline with no LiDAR map (NULL)."""
+    import torch
+    dev = torch.device("cuda:0")
+    ctx = S.Context(scene.W, scene.H, scene.D, params)
+    try:
+        out = torch.empty(scene.shape, dtype=torch.int16, device=dev)
+        ctx.compute(torch.from_numpy(scene.left).to(dev), torch.from_numpy(scene.right).to(dev), None, out)
+        ctx.sync()
+        return out.cpu().numpy(), ctx.stage(S.SGMF_STAGE_DSTAR), ctx.stage(S.SGMF_STAGE_DPRIME)
+    finally:
+        ctx.close()
+
+
+def _static(scene, params, dstar, dprime, lidar=True, free_check=False):
     import torch
     dev = torch.device("cuda:0")
     ds = torch.from_numpy(dstar).to(dev)
@@ -42,22 +56,31 @@ def _static(scene, params, dstar, dprime):
     li = torch.from_numpy(scene.lidar).to(dev)
     out = torch.full(scene.shape, 12345, dtype=torch.int16, device=dev)
     torch.cuda.synchronize()
-    S.sgmf_check_static(scene.W, scene.H, scene.D, params, ds.data_ptr(), dp.data_ptr(), li.data_ptr(),
-                        out.data_ptr(), None)
+    free0 = torch.cuda.mem_get_info()[0]
+    S.sgmf_check_static(scene.W, scene.H, scene.D, params, ds.data_ptr(), dp.data_ptr(),
+                        li.data_ptr() if lidar else None, out.data_ptr(), None)
     torch.cuda.synchronize()
+    if free_check:
+        # nothing was allocated on the device by the call
+        assert torch.cuda.mem_get_info()[0] == free0
     return out.cpu().numpy()
 
 
 def test_static_check_equals_pipeline_on_consecutive_calls(gpu):
     cases = [
-        (scenes.kitti(2300), S.Params()),                                  # 1242 x 375, D = 128
-        (scenes.tiny(1200), S.Params(consistency=S.SGMF_CHECK_LIDAR)),     # 256 x 128, D = 64
-        (scenes.kitti(2301), S.Params(tc=4, rc=9)),
+        (scenes.kitti(2300), S.Params(), True),                                   # 1242 x 375, D = 128
+        (scenes.tiny(1200), S.Params(consistency=S.SGMF_CHECK_LIDAR), True),      # 256 x 128, D = 64
+        (scenes.kitti(2301), S.Params(tc=4, rc=9), True),
+        (scenes.street(2310, 640, 480, 192), S.Params(), True),                   # 6 mask words a pixel
+        (scenes.street(2311, 640, 480, 256), S.Params(rc=7), True),               # 8 mask words a pixel
+        (scenes.kitti(2302), S.Params(consistency=S.SGMF_CHECK_STEREO), True),    # no box-OR
+        (scenes.tiny(1202), S.Params(consistency=S.SGMF_CHECK_NONE), True),
+        (scenes.kitti(2303), S.Params(), False),                                  # no LiDAR map
     ]
-    for scene, params in cases:
-        want, dstar, dprime = _pipeline(scene, params)
-        got = _static(scene, params, dstar, dprime)
-        np.testing.assert_array_equal(got, want, err_msg=scene.name)
+    for i, (scene, params, lidar) in enumerate(cases):
+        want, dstar, dprime = _pipeline(scene, params) if lidar else _pipeline_nolidar(scene, params)
+        got = _static(scene, params, dstar, dprime, lidar, free_check=i > 0)
+        np.testing.assert_array_equal(got, want, err_msg=f"case {i}: {scene.name}")
 
 
 def test_static_check_rejects_frames_beyond_its_array(gpu):
