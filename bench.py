@@ -352,6 +352,7 @@ def run_mixed(args, rank, world):
     for v, h in zip(views, hout):
         if not torch.equal(v[3].cpu(), h):
             raise RuntimeError("host copy of the output differs from the device buffer")
+    launch_cmp = launch_compare(m, scs, stream, flush) if args.launch_compare else None
     if rank != 0:
         m.close()
         return 0
@@ -371,9 +372,111 @@ def run_mixed(args, rank, world):
                 "frames_per_s": args.steps * len(scs) / dt},
         "gpu_launches": args.steps * m.launches(), "clocks": clk,
     }
+    if launch_cmp is not None:
+        line["launch_compare"] = launch_cmp
     print(json.dumps(line), flush=True)
     m.close()
     return 0
+
+
+def launch_compare(m, scs, stream, flush, reps: int = 5) -> dict:
+    """The same mixed batch as (a) the one-launch graph of class branches,
+    (b) one batched context per class, each on its own stream, without a
+    graph, (c) those contexts one after another, and (d) a graph of as many
+    empty kernel launches with the same branch structure (the launch floor).
+    (a) against (c) is the overlap the branches get; (a) against (b) what the
+    graph itself saves; a persistent kernel could at most remove the gaps
+    that separate (a) from the busy time of its kernels."""
+    import numpy as np
+    import torch
+    from paper_2504_05148_gb300 import sgmf
+    dev = stream.device
+    cls = m.classes()
+    order = {}
+    for i, s in enumerate(scs):
+        order.setdefault((s.W, s.H, s.D), []).append(i)
+    ctxs, streams, bufs = [], [], []
+    for (sh, nf, t) in cls:
+        W_, H_, D_ = sh
+        idx = order[(W_, H_, D_)]
+        st = torch.cuda.Stream(device=dev)
+        c = sgmf.Context(W_, H_, D_, stream=st, max_batch=nf)
+        sgmf.sgmf_set_tuning(c.handle, t[0], t[1], t[2])
+        l = torch.from_numpy(np.stack([scs[i].left for i in idx])).to(dev)
+        r = torch.from_numpy(np.stack([scs[i].right for i in idx])).to(dev)
+        li = torch.from_numpy(np.stack([scs[i].lidar for i in idx])).to(dev)
+        o = torch.empty((nf, H_, W_), dtype=torch.int16, device=dev)
+        ctxs.append(c)
+        streams.append(st)
+        bufs.append((l, r, li, o))
+
+    def timed(body):
+        ts = []
+        for k in range(reps + 1):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            body(a)
+            b.record(stream)
+            b.synchronize()
+            if k:
+                ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    def graph(a):
+        m.launch(stream)
+
+    def concurrent(a):
+        for st in streams:
+            st.wait_event(a)
+        for c, (l, r, li, o) in zip(ctxs, bufs):
+            c.compute(l, r, li, o)
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
+
+    def serial(a):
+        prev = a
+        for c, st, (l, r, li, o) in zip(ctxs, streams, bufs):
+            st.wait_event(prev)
+            c.compute(l, r, li, o)
+            prev = torch.cuda.Event()
+            prev.record(st)
+        stream.wait_event(prev)
+
+    # the launch floor: as many empty kernels as the graph holds, in the same branches
+    nk = [c.launches_per_compute() for c in ctxs]
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    dummy = torch.zeros(1, device=dev)
+    with torch.cuda.graph(g, stream=cap):
+        fork = torch.cuda.Event()
+        fork.record(cap)
+        joins = []
+        for n_, st in zip(nk, streams):
+            st.wait_event(fork)
+            with torch.cuda.stream(st):
+                for _ in range(n_):
+                    dummy.add_(0)
+            e = torch.cuda.Event()
+            e.record(st)
+            joins.append(e)
+        for e in joins:
+            cap.wait_event(e)
+
+    def empty(a):
+        g.replay()
+
+    with torch.cuda.stream(stream):
+        res = {"graph_ms": timed(graph), "streams_no_graph_ms": timed(concurrent), "classes_serial_ms": timed(serial),
+               "empty_graph_same_launches_ms": timed(empty)}
+    res["kernels_in_graph"] = int(sum(nk))
+    for c in ctxs:
+        c.close()
+    return res
 
 
 SERVE_CAMERAS = ((1242, 375, 128, 30.0), (1242, 375, 128, 20.0), (640, 480, 64, 25.0), (640, 480, 64, 15.0),
@@ -473,22 +576,23 @@ def run_learned(args, rank, world):
     dr = [stack(1, g) for g in groups]
     dli = [stack(2, g) for g in groups]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    bands = tuple(int(b) for b in args.bands.split(",")) if args.bands else (args.band,)
+    mk = lambda: bandnet.LearnedSGM(W_, H_, D_, net, bands=bands, conf_min=args.conf_min,
+                                    fallback_frac=args.fallback_frac, max_batch=nb)
     if args.no_plain:
         # the learned path alone (a small device footprint, for profiling)
-        learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
-                                     fallback_frac=args.fallback_frac, max_batch=nb)
+        learned = mk()
         out = torch.empty((nb, H_, W_), dtype=torch.int16, device=dev)
         for _ in range(max(args.steps_learned, 1) + 1):
             for i in range(len(groups)):
                 learned.compute(dl[i], dr[i], dli[i], out)
         learned.sync()
         print(json.dumps({"metric": "learned band path only (profiling run)", "frames": len(frames),
-                          "stats": learned.stats}), flush=True)
+                          "bands": list(bands)}), flush=True)
         learned.close()
         return 0
     plain = sgmf.Context(W_, H_, D_, max_batch=nb)
-    learned = bandnet.LearnedSGM(W_, H_, D_, net, band=args.band, conf_min=args.conf_min,
-                                 fallback_frac=args.fallback_frac, max_batch=nb)
+    learned = mk()
     outp = [torch.empty((nb, H_, W_), dtype=torch.int16, device=dev) for _ in groups]
     outl = [torch.empty((nb, H_, W_), dtype=torch.int16, device=dev) for _ in groups]
 
@@ -509,7 +613,6 @@ def run_learned(args, rank, world):
         run_p(i)
         run_l(i)
     torch.cuda.synchronize()
-    learned.stats = {k: 0 for k in learned.stats}
     clocks = ClockSampler(0)
     clocks.start()
     tp, tl = [], []
@@ -518,9 +621,19 @@ def run_learned(args, rank, world):
             tp.append(timed(run_p, i))
             tl.append(timed(run_l, i))
     clk = clocks.stop()
-    # per-stage split of the learned path and per-kernel times of both (one more profiled call each)
+    # the per-frame decisions (each group once more), the per-stage split of the
+    # learned path and the per-kernel times of both (one more profiled call each)
+    gates, uncs = [], []
+    for i in range(len(groups)):
+        run_l(i)
+        g_, u_ = learned.decision()
+        gates.append(g_)
+        uncs.append(u_)
+    gates = np.concatenate(gates)
+    uncs = np.concatenate(uncs, axis=1)
     plain.set_profiling(True)
-    learned.banded.set_profiling(True)
+    for c in learned.ctxs:
+        c.set_profiling(True)
     learned.marks = []
     timed(run_p, 0)
     timed(run_l, 0)
@@ -528,26 +641,29 @@ def run_learned(args, rank, world):
     learned.marks = None
     stages = {ev[k][0]: ev[k - 1][1].elapsed_time(ev[k][1]) for k in range(1, len(ev))}
     kp = {k: round(v, 4) for k, v in plain.kernel_times()}
-    kl = {k: round(v, 4) for k, v in learned.banded.kernel_times()}
+    kl = {f"B{b}": {k: round(v, 4) for k, v in c.kernel_times()} for b, c in zip(bands, learned.ctxs)}
     plain.set_profiling(False)
-    learned.banded.set_profiling(False)
+    for c in learned.ctxs:
+        c.set_profiling(False)
     plain.sync()
     learned.sync()
     dis = [bandnet.disagreement(outl[g][j].cpu().numpy(), outp[g][j].cpu().numpy())
            for g in range(len(groups)) for j in range(nb)]
     whd = W_ * H_ * D_ * nb
     vp, vl = whd / (np.mean(tp) * 1e-3), whd / (np.mean(tl) * 1e-3)
-    st = learned.stats
+    tiles = learned.th * learned.tw
     line = {
         "metric": "W*H*D/s at 1920x1080 D=256, learned band vs plain full range", "value": vl, "unit": UNIT,
         "n_gpus": 1, "steps": len(tl), "warmup": 1, "ms_per_step": float(np.mean(tl)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16 (SGM), bf16 (network)",
         "data": "synthetic",
-        "learned": {"W*H*D/s": vl, "ms_per_frame": float(np.mean(tl)) / nb, "band": args.band,
+        "learned": {"W*H*D/s": vl, "ms_per_frame": float(np.mean(tl)) / nb, "bands": list(bands),
                     "speedup_vs_plain": vl / vp, "px_off_by_more_than_1": float(np.mean(dis)),
                     "px_off_by_more_than_1_max_frame": float(np.max(dis)),
-                    "fallback_rate": st["fallback_frames"] / max(st["frames"], 1),
-                    "uncertain_tile_fraction": st["uncertain_tiles"] / max(st["tiles"], 1),
+                    "frames_per_path": {("plain" if v == learned.PLAIN else f"B{bands[v]}"): int((gates == v).sum())
+                                        for v in range(len(bands) + 1)},
+                    "fallback_rate": float((gates == learned.PLAIN).mean()),
+                    "uncertain_tile_fraction": {f"B{b}": float(uncs[k].mean() / tiles) for k, b in enumerate(bands)},
                     "conf_min": args.conf_min, "fallback_frac": args.fallback_frac,
                     "stage_ms": {k: round(v, 4) for k, v in stages.items()}, "kernel_ms": kl},
         "plain": {"W*H*D/s": vp, "ms_per_frame": float(np.mean(tp)) / nb, "kernel_ms": kp},
@@ -562,6 +678,42 @@ def run_learned(args, rank, world):
     learned.close()
     plain.close()
     return 0
+
+
+# Short runs of the other workloads, reported inside the default line
+# (bounded: a few seconds of GPU time each, plus scene generation).
+EXTRAS = {
+    "mixed": ["--workload", "mixed", "--steps", "5", "--warmup", "3"],
+    "serve": ["--workload", "serve", "--serve-seconds", "3"],
+    "learned": ["--workload", "learned", "--eval-frames", "8", "--learned-batch", "8", "--steps-learned", "2"],
+}
+EXTRA_KEYS = {
+    "mixed": ("metric", "value", "unit", "ms_per_step", "frames_per_s", "e2e", "gpu_launches", "clocks", "config"),
+    "serve": ("metric", "value", "unit", "latency_ms", "saturated", "server", "gpu_launches", "clocks", "config"),
+    "learned": ("metric", "value", "unit", "ms_per_step", "learned", "plain", "clocks", "config"),
+}
+
+
+def run_extras(args) -> dict:
+    """Each extra workload in its own process (a fresh CUDA context, the main
+    run's memory released), its JSON line cut to the keys above."""
+    out = {}
+    for name, argv in EXTRAS.items():
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__)] + argv, capture_output=True, text=True,
+                               timeout=args.extras_timeout, cwd=ROOT)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"error": f"rc={r.returncode}: {(r.stderr or r.stdout)[-400:]}"}
+                continue
+            d = json.loads(lines[-1])
+            out[name] = {k: d[k] for k in EXTRA_KEYS[name] if k in d}
+            out[name]["cmd"] = "python bench.py " + " ".join(argv)
+            out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": f"timed out after {args.extras_timeout} s"}
+    return out
 
 
 def main():
@@ -579,12 +731,19 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="learned workload: skip the plain comparison")
     ap.add_argument("--steps-learned", type=int, default=3)
     ap.add_argument("--band", type=int, default=64, choices=[64, 128])
+    ap.add_argument("--bands", default=None, metavar="B1,B2",
+                    help="learned workload: band widths a frame may take (narrowest acceptable wins)")
     ap.add_argument("--conf-min", type=float, default=0.3)
     ap.add_argument("--fallback-frac", type=float, default=0.25)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--launch-compare", action="store_true",
+                    help="mixed workload: also time streams without a graph, classes one by one, and the launch floor")
     ap.add_argument("--mixed-distinct", type=int, default=3,
                     help="distinct generated pairs per shape in the mixed batch (reused cyclically)")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the short mixed / serve / learned runs in the line")
+    ap.add_argument("--extras-timeout", type=float, default=300.0)
     ap.add_argument("--tuning", default=None, metavar="LINE_WARPS,COST_PX,SWEEP",
                     help="kitti workload: this launch tuning instead of the autotuner")
     args = ap.parse_args()
@@ -839,6 +998,7 @@ def main():
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world > 1 and False):
         cpu = time_oracle(frames)
         cpu["all_cores"] = time_oracle_all_cores(frames, os.cpu_count() or 1)
+    extras = {} if args.no_extras or world > 1 else run_extras(args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -855,6 +1015,7 @@ def main():
         "kernel_ms_avg": {k: round(v, 4) for k, v in sorted(avg.items())},
         "paper_context": {"sdsgm_ms_per_frame": 50, "hardware": "Jetson Orin NX 16GB", "data": "KITTI 141"},
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg:

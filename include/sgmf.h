@@ -352,12 +352,23 @@ sgmf_status sgmf_bn_loss(long long npix, int max_disp, const float *out, const i
 sgmf_status sgmf_bn_adam(int count, float *w, float *m, float *v, const float *g, float lr, float b1, float b2,
                          float eps, int step, uint16_t *w_bf16, void *stream);
 
+/* Training batch: dst row i = src row idx[i] for i < n <= 65535 (rows of
+ * row_bytes bytes, a multiple of 4; src and dst 4-byte aligned; idx device
+ * int32; src holds `rows` rows, and an entry outside [0, rows) leaves its
+ * destination row untouched).  Errors: SGMF_ERR_ARG. */
+sgmf_status sgmf_bn_gather(int n, const int *idx, long long rows, long long row_bytes, const void *src, void *dst,
+                           void *stream);
+
+/* bf16 copy (round to nearest, ties to even) of count f32 weights. */
+sgmf_status sgmf_bn_to_bf16(int count, const float *w, uint16_t *w_bf16, void *stream);
+
 /* Band starts from the network output out (f32 [n][H4][W4][32]) for a
  * banded context of width `band`: per 8 x 8 tile the union [lo, hi] of the
  * pixels' bands [c - w, c + w], start round((lo + hi) / 2) - band / 2 clamped
  * to [0, max_disp - band] into lo_tiles int16 [n][ceil(H/8)][ceil(W/8)];
- * *uncertain += tiles whose smallest confidence is below conf_min or whose
- * union is wider than the band. */
+ * uncertain[f] (n device ints, zeroed by the caller) += the tiles of frame f
+ * whose smallest confidence is below conf_min or whose union is wider than
+ * the band. */
 sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp, int band, float conf_min, const float *out,
                           int16_t *lo_tiles, int *uncertain, void *stream);
 
@@ -365,6 +376,27 @@ sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp, int band, 
  * uint16 H x W x band (cell j = disparity lo_p + j; SUM needs no
  * sgmf_set_debug there).  The context's band width (0 for a plain context): */
 int sgmf_band_width(const sgmf_ctx *c);
+
+/* The per-frame choice among band widths and the plain method, made on the
+ * device (no host round trip): gate[f] = value when frame f has at most
+ * max_frac * tiles uncertain tiles (uncertain: the counts of sgmf_bn_tiles
+ * for one band width), else `otherwise` (otherwise < 0 keeps gate[f]).
+ * Called once per band width, widest first with otherwise = the plain
+ * method's value, then narrower ones with otherwise = -1, the narrowest
+ * acceptable width wins.  Each context then runs only its frames
+ * (sgmf_set_gate).  Errors: SGMF_ERR_ARG. */
+sgmf_status sgmf_bn_decide(int n, int tiles, float max_frac, const int *uncertain, int value, int otherwise,
+                           int *gate, void *stream);
+
+/* Per-frame gating of a context's kernels (no counterpart in the paper):
+ * with gate (device int array, one word per frame of a compute call, frame i
+ * at gate[i]) non-NULL, every kernel the context launches does nothing for
+ * frame i unless gate[i] == run; NULL runs every frame (the default).  The
+ * launches still happen (a skipped frame costs only its CTAs' start), so
+ * several contexts can share one batch's frames by a decision that a kernel
+ * wrote, without the host waiting for it.  The gate memory must stay valid
+ * while launches that read it are in flight.  Errors: SGMF_ERR_ARG. */
+sgmf_status sgmf_set_gate(sgmf_ctx *c, const int *gate, int run);
 
 /* ---- Launch tuning (no counterpart in the paper) -----------------------
  * Launch shapes only: every choice gives bit-identical results. */

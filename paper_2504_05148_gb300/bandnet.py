@@ -9,10 +9,11 @@ calls.
 
 Inference (LearnedSGM): the banded context's front half (ingest, census,
 semidensification) gives d-hat; the network turns it into one band start
-per 8 x 8 tile; if more than `fallback_frac` of the tiles are uncertain
-(low confidence or a union of pixel bands wider than the band), the frame
-falls back to the plain full-range method, else the banded back half
-finishes it.
+per 8 x 8 tile for each band width; per frame a kernel picks the narrowest
+width with at most `fallback_frac` uncertain tiles (low confidence or a
+union of pixel bands wider than the band), else the plain full-range
+method; each context then runs only its frames (per-frame gates on the
+device, no host round trip).
 """
 from __future__ import annotations
 
@@ -66,13 +67,8 @@ class BandNet:
         self._sync_bf16()
 
     def _sync_bf16(self):
-        # bf16 copy of the master weights through a zero-rate Adam step is not
-        # exact (it would move the moments): pack from a bf16 rounding instead
-        import torch
-        f = self.master.detach().cpu().numpy().astype(np.float32)
-        u = f.view(np.uint32).astype(np.uint64)
-        r = (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
-        self.wbf.copy_(torch.from_numpy(r.view(np.int16)))
+        # the bf16 copy of the master weights (a library kernel), then the operand images
+        S.sgmf_bn_to_bf16(LAYERS * PSZ, self.master.data_ptr(), self.wbf.data_ptr())
         self.repack()
 
     def w_ptr(self, l):
@@ -131,11 +127,25 @@ class BandNet:
             raise RuntimeError("a bounded wait in a network kernel gave up")
 
     def save(self, path):
-        np.savez(path, master=self.master.cpu().numpy())
+        """The fp32 master weights and the optimiser state (Adam moments and
+        step count), so that training can resume exactly where it stopped."""
+        np.savez(path, master=self.master.cpu().numpy(), adam_m=self.m.cpu().numpy(), adam_v=self.v.cpu().numpy(),
+                 adam_t=np.int64(self.t))
 
     def load(self, path):
+        """Weights, and the optimiser state when the file holds it (older
+        files hold the weights only: the moments start at zero)."""
         import torch
-        self.master.copy_(torch.from_numpy(np.load(path)["master"]))
+        z = np.load(path)
+        self.master.copy_(torch.from_numpy(z["master"]))
+        if "adam_m" in z.files:
+            self.m.copy_(torch.from_numpy(z["adam_m"]))
+            self.v.copy_(torch.from_numpy(z["adam_v"]))
+            self.t = int(z["adam_t"])
+        else:
+            self.m.zero_()
+            self.v.zero_()
+            self.t = 0
         self._sync_bf16()
 
 
@@ -188,13 +198,22 @@ def build_training_set(n_pairs: int, seed0: int = 100000, W: int = 1242, H: int 
     return x_all, lohi_all, counts
 
 
+def batch_indices(seed: int, step: int, n: int, batch: int) -> np.ndarray:
+    """The training pairs of one step: a function of (seed, step) alone, so a
+    run resumed at any step draws the batches an uninterrupted one would."""
+    return np.random.default_rng([seed, step]).choice(n, size=batch, replace=False)
+
+
 def train(net: BandNet, x_all, lohi_all, counts, steps: int, batch: int = 16, lr: float = 2e-3, seed: int = 0,
-          log_every: int = 100, D: int = 128):
-    """Adam on the band loss; returns the loss history (one value per step)."""
+          log_every: int = 100, D: int = 128, start: int = 0, stop: int | None = None):
+    """Adam on the band loss over steps [start, stop) of a run of `steps`
+    steps (the learning-rate schedule follows `steps`); returns the loss
+    history.  With the optimiser state saved by BandNet.save, a run stopped
+    at step k and resumed with start = k gives the uninterrupted run's weights."""
     import torch
     dev = torch.device("cuda")
     N, H4, W4, _ = x_all.shape
-    rng = np.random.default_rng(seed)
+    stop = steps if stop is None else stop
     acts = [None] + [torch.empty((batch, H4, W4, C), dtype=torch.int16, device=dev) for _ in range(LAYERS - 1)]
     out = torch.empty((batch, H4, W4, C), dtype=torch.float32, device=dev)
     grad = torch.empty((batch, H4, W4, C), dtype=torch.int16, device=dev)
@@ -203,12 +222,14 @@ def train(net: BandNet, x_all, lohi_all, counts, steps: int, batch: int = 16, lr
     lb = torch.empty((batch, H4, W4, 2), dtype=torch.int16, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ti = torch.empty(batch, dtype=torch.int32, device=dev)
+    xrow, lrow = H4 * W4 * C * 2, H4 * W4 * 2 * 2
     hist = []
-    for st in range(steps):
-        idx = rng.choice(N, size=batch, replace=False)
-        ti = torch.from_numpy(idx).to(dev)
-        torch.index_select(x_all, 0, ti, out=xb)
-        torch.index_select(lohi_all, 0, ti, out=lb)
+    for st in range(start, stop):
+        idx = batch_indices(seed, st, N, batch)
+        ti.copy_(torch.from_numpy(idx.astype(np.int32)))
+        S.sgmf_bn_gather(batch, ti.data_ptr(), N, xrow, x_all.data_ptr(), xb.data_ptr())
+        S.sgmf_bn_gather(batch, ti.data_ptr(), N, lrow, lohi_all.data_ptr(), lb.data_ptr())
         cnt.fill_(int(counts[idx].sum()))
         loss.zero_()
         net.forward(xb, batch, H4, W4, acts, out)
@@ -252,24 +273,35 @@ def evaluate(net: BandNet, x_all, lohi_all, counts, batch: int = 16, D: int = 12
 # ---- inference ------------------------------------------------------------------------
 
 class LearnedSGM:
-    """The banded method driven by the network, with the plain method as the
-    per-frame fallback."""
+    """The banded method driven by the network.  Every frame takes the
+    narrowest band width whose proposal it trusts (at most `fallback_frac`
+    of its tiles uncertain) and falls back to the plain full-range method
+    when none qualifies.  The choice is made per frame by a kernel; every
+    context then runs only its own frames (sgmf_set_gate), so a call never
+    waits for the proposal on the host."""
 
     def __init__(self, W: int, H: int, D: int, net: BandNet, band: int = 64, params=None, max_batch: int = 1,
-                 conf_min: float = 0.5, fallback_frac: float = 0.02, sweep: bool | None = None):
+                 conf_min: float = 0.5, fallback_frac: float = 0.02, sweep: bool | None = None,
+                 bands: tuple | None = None):
         import torch
-        self.W, self.H, self.D, self.band = W, H, D, band
+        self.W, self.H, self.D = W, H, D
+        self.bands = tuple(sorted(bands if bands is not None else (band,)))
+        self.band = self.bands[0]
         self.net = net
         self.conf_min, self.fallback_frac = conf_min, fallback_frac
-        self.banded = S.Context(W, H, D, params, band=band, max_batch=max_batch)
+        # one banded context per width (gate value = its index), the plain one last
+        self.ctxs = [S.Context(W, H, D, params, band=b, max_batch=max_batch) for b in self.bands]
+        self.banded = self.ctxs[0]          # runs the front half that feeds the network
         # the cluster sweep for the banded walks where it fits; it needs several
         # frames per call to fill the GPU (one cluster per frame and direction)
         if sweep if sweep is not None else max_batch >= 4:
-            try:
-                S.sgmf_set_tuning(self.banded.handle, 4, 128, 1)
-            except S.SgmfError:
-                pass
+            for c in self.ctxs:
+                try:
+                    S.sgmf_set_tuning(c.handle, 4, 128, 1)
+                except S.SgmfError:
+                    pass
         self.plain = S.Context(W, H, D, params, max_batch=max_batch)
+        self.PLAIN = len(self.bands)
         dev = torch.device("cuda")
         self.H4, self.W4 = _q(4, H), _q(4, W)
         self.th, self.tw = _q(S.BAND_TILE, H), _q(S.BAND_TILE, W)
@@ -278,16 +310,18 @@ class LearnedSGM:
         self.acts = [None] + [torch.empty((n, self.H4, self.W4, C), dtype=torch.int16, device=dev)
                               for _ in range(LAYERS - 1)]
         self.out = torch.empty((n, self.H4, self.W4, C), dtype=torch.float32, device=dev)
-        self.lo = torch.empty((n, self.th, self.tw), dtype=torch.int16, device=dev)
-        self.unc = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.stats = {"frames": 0, "fallback_frames": 0, "uncertain_tiles": 0, "tiles": 0}
+        self.lo = [torch.empty((n, self.th, self.tw), dtype=torch.int16, device=dev) for _ in self.bands]
+        self.unc = torch.zeros((len(self.bands), n), dtype=torch.int32, device=dev)
+        self.gate = torch.zeros(n, dtype=torch.int32, device=dev)
         self.marks = None          # set to a list to receive (name, cuda event) pairs per compute
+        self.last_n = 0
 
     def compute(self, left, right, lidar, out):
         """left/right uint8, lidar float32, out int16: (n, H, W) CUDA tensors.
-        Returns True when the batch fell back to the plain method."""
+        Enqueues everything; the per-frame choice stays on the device."""
         import torch
         n = left.shape[0] if left.dim() == 3 else 1
+        tiles = self.th * self.tw
 
         def mark(name):
             if self.marks is not None:
@@ -296,6 +330,8 @@ class LearnedSGM:
                 self.marks.append((name, e))
 
         mark("start")
+        for c in self.ctxs:                 # the front half runs on every frame
+            S.sgmf_set_gate(c.handle, None, 0)
         S.sgmf_compute_front(self.banded.handle, n, left.data_ptr(), right.data_ptr(),
                              lidar.data_ptr() if lidar is not None else None)
         mark("front")
@@ -308,29 +344,42 @@ class LearnedSGM:
                            self.net.b_ptr(l), not last, None, None if last else self.acts[l + 1].data_ptr(),
                            self.out.data_ptr() if last else None, self.net.err.data_ptr())
         self.unc.zero_()
-        S.sgmf_bn_tiles(n, self.W, self.H, self.D, self.band, self.conf_min, self.out.data_ptr(), self.lo.data_ptr(),
-                        self.unc.data_ptr())
+        for i, b in enumerate(self.bands):
+            S.sgmf_bn_tiles(n, self.W, self.H, self.D, b, self.conf_min, self.out.data_ptr(), self.lo[i].data_ptr(),
+                            self.unc[i].data_ptr())
+        # widest band first (else the plain method), then narrower ones replace it where acceptable
+        for i in range(len(self.bands) - 1, -1, -1):
+            S.sgmf_bn_decide(n, tiles, self.fallback_frac, self.unc[i].data_ptr(), i,
+                             self.PLAIN if i == len(self.bands) - 1 else -1, self.gate.data_ptr())
         mark("network")
-        unc = int(self.unc.item())     # waits for the proposal
-        tiles = n * self.th * self.tw
-        self.stats["frames"] += n
-        self.stats["uncertain_tiles"] += unc
-        self.stats["tiles"] += tiles
-        if unc > self.fallback_frac * tiles:
-            self.stats["fallback_frames"] += n
+        for i, c in enumerate(self.ctxs):
+            if i > 0:                       # the other widths run their own front half on their frames
+                S.sgmf_set_gate(c.handle, self.gate.data_ptr(), i)
+                S.sgmf_compute_front(c.handle, n, left.data_ptr(), right.data_ptr(),
+                                     lidar.data_ptr() if lidar is not None else None)
+            S.sgmf_set_gate(c.handle, self.gate.data_ptr(), i)
+            S.sgmf_compute_banded_back(c.handle, n, self.lo[i].data_ptr(), out.data_ptr())
+        if self.fallback_frac < 1.0:         # else no frame can fall back: nothing to launch
+            S.sgmf_set_gate(self.plain.handle, self.gate.data_ptr(), self.PLAIN)
             self.plain.compute(left, right, lidar, out)
-            return True
-        S.sgmf_compute_banded_back(self.banded.handle, n, self.lo.data_ptr(), out.data_ptr())
         mark("back")
-        return False
+        self.last_n = n
+
+    def decision(self):
+        """(width index or PLAIN per frame, uncertain tiles per width and frame)
+        of the last call; waits for it."""
+        n = self.last_n
+        return self.gate[:n].cpu().numpy().copy(), self.unc[:, :n].cpu().numpy().copy()
 
     def sync(self):
-        self.banded.sync()
+        for c in self.ctxs:
+            c.sync()
         self.plain.sync()
         self.net.check()
 
     def close(self):
-        self.banded.close()
+        for c in self.ctxs:
+            c.close()
         self.plain.close()
 
 
@@ -346,14 +395,19 @@ def disagreement(learned: np.ndarray, plain: np.ndarray) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the band-proposal network on generated street pairs")
-    ap.add_argument("--pairs", type=int, default=2000)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--heldout", type=int, default=256, help="pairs of unseen seeds for the held-out loss")
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=0, help="batch-order seed")
+    ap.add_argument("--checkpoint-every", type=int, default=1000)
+    ap.add_argument("--resume", action="store_true", help="continue the run saved in --out (weights + Adam state)")
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                                                   "bandnet_street.npz"))
     args = ap.parse_args(argv)
+    import json
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.workers) as pool:
@@ -361,14 +415,33 @@ def main(argv=None):
         _build.build()
         t0 = time.time()
         x_all, lohi_all, counts = build_training_set(args.pairs, pool=pool)
-        print(f"training set: {args.pairs} pairs in {time.time() - t0:.0f} s", flush=True)
+        gen_s = time.time() - t0
+        print(f"training set: {args.pairs} pairs in {gen_s:.0f} s", flush=True)
+        x_h, lohi_h, counts_h = build_training_set(args.heldout, seed0=200000, pool=pool)
     net = BandNet(seed=1)
+    start = 0
+    if args.resume and os.path.exists(args.out):
+        net.load(args.out)
+        start = net.t
+        print(f"resuming at step {start}", flush=True)
+    held0 = evaluate(net, x_h, lohi_h, counts_h)
     t0 = time.time()
-    hist = train(net, x_all, lohi_all, counts, args.steps, args.batch, args.lr)
-    print(f"trained {args.steps} steps in {time.time() - t0:.1f} s; loss {hist[0][1]:.4f} -> {hist[-1][1]:.4f}",
-          flush=True)
-    os.makedirs(os.path.dirname(args.out), exist_ok=True)
-    net.save(args.out)
+    hist = []
+    for a in range(start, args.steps, args.checkpoint_every):
+        b = min(args.steps, a + args.checkpoint_every)
+        hist += train(net, x_all, lohi_all, counts, args.steps, args.batch, args.lr, seed=args.seed, start=a, stop=b)
+        os.makedirs(os.path.dirname(args.out), exist_ok=True)
+        net.save(args.out)
+        print(f"checkpoint at step {b}: held-out loss {evaluate(net, x_h, lohi_h, counts_h):.4f}", flush=True)
+    train_s = time.time() - t0
+    held = evaluate(net, x_h, lohi_h, counts_h)
+    log = {"pairs": args.pairs, "heldout_pairs": args.heldout, "steps": args.steps, "batch": args.batch, "lr": args.lr,
+           "seed": args.seed, "generation_s": round(gen_s, 1), "train_s": round(train_s, 1),
+           "heldout_loss_start": held0, "heldout_loss_end": held,
+           "loss_every_10_steps": [[int(st), round(v, 5)] for st, v in hist]}
+    with open(os.path.splitext(args.out)[0] + "_train.json", "w") as fh:
+        json.dump(log, fh)
+    print(f"trained {args.steps - start} steps in {train_s:.1f} s; held-out loss {held0:.4f} -> {held:.4f}", flush=True)
     print("saved", args.out, flush=True)
 
 

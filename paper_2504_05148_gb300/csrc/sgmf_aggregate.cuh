@@ -371,6 +371,7 @@ struct LineArgs {
   StepConsts sc;
   const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]
   int tw, th;
+  const int *gate;        // per-frame gate words of the launch's frames, or null
 };
 
 template <int CPL, bool S8, int NWARP>
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(32 * NWARP) k_agg_lines(const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> 4, lig = lane & 15;
   const int f = blockIdx.y;
+  if (gated_off(a.gate ? a.gate + f : nullptr, a.k.gate_run)) return;
   const int W = a.k.W, H = a.k.H;
   const size_t fcells = frame_cells(a.k);
   const uint8_t *cost = a.cost + f * fcells;
@@ -638,6 +640,7 @@ struct RowArgs {
   StepConsts sc;
   const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]
   int tw, th;
+  const int *gate;        // per-frame gate words of the launch's frames, or null
 };
 
 template <int CPL, bool S8, int NP>
@@ -863,6 +866,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
   uint32_t *merge = reinterpret_cast<uint32_t *>(smem + S * CF::kStage + S * 8);
   const int lane = threadIdx.x & 31, grp = lane >> 4, lig = lane & 15;
   const int y = blockIdx.x, f = blockIdx.y;
+  if (gated_off(a.gate ? a.gate + f : nullptr, a.k.gate_run)) return;
   RowGeom g;
   g.W = a.k.W;
   g.D = a.k.D;
@@ -1094,6 +1098,7 @@ cudaError_t launch_lines_t(const KParams &k, const Buffers &b, int nf, cudaStrea
   a.lo = k.band ? b.band_lo : nullptr;
   a.tw = k.tw;
   a.th = k.th;
+  a.gate = b.gate;
   // the three families are independent: one launch each, back to back
   cudaError_t e = launch_line_family<CPL, S8, 0>(a, nf, s);
   if (e != cudaSuccess || k.num_paths != 8) return e;
@@ -1133,6 +1138,7 @@ cudaError_t launch_rows_t(const KParams &k, const Buffers &b, int nf, cudaStream
   a.lo = b.band_lo;
   a.tw = k.tw;
   a.th = k.th;
+  a.gate = b.gate;
   if (k.band) {
     if constexpr (CPL <= 8) {
       if (k.sweep) return launch_rows_v<CPL, S8, 2, true, true>(a, nf, s);

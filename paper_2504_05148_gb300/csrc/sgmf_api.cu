@@ -31,13 +31,11 @@ struct sgmf_ctx {
   bool sweep_ok = false;       // the row-synchronous sweep can run this shape on this device (8 paths)
   int sweep_slots = 0;         // sweep clusters the device holds at once
   size_t spill_bytes = 0;
-  // with the sweep, a batch goes through in parts: part i's sweep runs on
-  // the context's stream while part i+1's front stages (ingest .. cost) run
-  // on `front` and part i's row kernel and check on `side`
+  // with the sweep, a batch goes through in parts: part i's row kernel and
+  // check run on this second stream while part i + 1 is in the sweep
   static constexpr int kMaxParts = 8;
-  cudaStream_t side = nullptr, front = nullptr;
+  cudaStream_t side = nullptr;
   cudaEvent_t ev_part[kMaxParts] = {};
-  cudaEvent_t ev_front[kMaxParts] = {};
   cudaEvent_t ev_rows = nullptr, ev_in = nullptr;
   size_t bytes = 0;
   std::string err;
@@ -205,19 +203,16 @@ static void free_all(sgmf_ctx *c) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
-  for (cudaEvent_t *arr : {c->ev_part, c->ev_front})
-    for (int i = 0; i < sgmf_ctx::kMaxParts; ++i) {
-      if (arr[i]) cudaEventDestroy(arr[i]);
-      arr[i] = nullptr;
-    }
+  for (int i = 0; i < sgmf_ctx::kMaxParts; ++i) {
+    if (c->ev_part[i]) cudaEventDestroy(c->ev_part[i]);
+    c->ev_part[i] = nullptr;
+  }
   for (cudaEvent_t *e : {&c->ev_rows, &c->ev_in}) {
     if (*e) cudaEventDestroy(*e);
     *e = nullptr;
   }
-  for (cudaStream_t *st : {&c->side, &c->front}) {
-    if (*st) cudaStreamDestroy(*st);
-    *st = nullptr;
-  }
+  if (c->side) cudaStreamDestroy(c->side);
+  c->side = nullptr;
 }
 
 // test hook (sgmf_debug_fail_alloc): allocations until the injected failure
@@ -327,12 +322,10 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     c->sweep_ok = c->k.sweep_cs > 0;
     bool ok = !(c->sweep_ok && c->nb >= 2) ||
               (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
-               cudaStreamCreateWithFlags(&c->front, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess);
     for (int i = 0; ok && c->side && i < sgmf_ctx::kMaxParts; ++i)
-      ok = cudaEventCreateWithFlags(&c->ev_part[i], cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&c->ev_front[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = cudaEventCreateWithFlags(&c->ev_part[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       c->sweep_slots = 0;        // no parts: everything on the context's stream
@@ -388,6 +381,13 @@ extern "C" sgmf_status sgmf_get_params(const sgmf_ctx *c, sgmf_params *p) {
   return SGMF_OK;
 }
 
+extern "C" sgmf_status sgmf_set_gate(sgmf_ctx *c, const int *gate, int run) {
+  if (!c) return SGMF_ERR_ARG;
+  c->b.gate = gate;
+  c->k.gate_run = run;
+  return SGMF_OK;
+}
+
 extern "C" sgmf_status sgmf_set_wait_limit(sgmf_ctx *c, int which, long long polls) {
   if (!c) return SGMF_ERR_ARG;
   if (which != SGMF_WAIT_CENSUS) return fail(c, SGMF_ERR_ARG, "sgmf_set_wait_limit: unknown wait %d", which);
@@ -407,12 +407,11 @@ static bool need_boxc(const KParams &k) { return k.consistency == SGMF_CHECK_STE
 static bool use_sweep(const sgmf_ctx *c) { return c->k.sweep && c->k.num_paths == 8 && c->sweep_ok; }
 
 // Frames per part when a sweep batch of n frames goes through in parts (0:
-// one part).  A part's row kernel and check run on the side stream, and the
-// next part's front stages on the front stream, beside the part's sweep:
-// they fill the SMs (and the register room) the sweep clusters leave, and
-// the next sweep finds its cost volume ready.  Every part but the last is
-// one wave of sweep clusters (2 m cluster jobs, the resident count or its
-// smallest even multiple), so the parts add no wave; at most kMaxParts parts.
+// one part).  A part's row kernel and check run on the side stream beside
+// the next part's sweep, filling the SMs (and the register room) the sweep
+// clusters leave.  Every part but the last is one wave of sweep clusters
+// (2 m cluster jobs, the resident count or its smallest even multiple), so
+// the parts add no wave; at most kMaxParts parts.
 static int sweep_part(const sgmf_ctx *c, int n) {
   if (!c->k.parts || !c->side || c->sweep_slots < 1 || n < 2) return 0;
   int m = c->sweep_slots % 2 == 0 ? c->sweep_slots / 2 : c->sweep_slots;   // 2 m % slots == 0
@@ -436,14 +435,14 @@ static int front_launches(const KParams &k) {
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
   if (!c) return 0;
   // front stages, one line launch per family (one sweep launch for all six directions), rows, consistency
-  // (a sweep batch in parts launches all of them once per part; counted for a full batch)
-  const int per = front_launches(c->k) + (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1) + 2;
+  // (a sweep batch in parts launches the sweep, rows and check once per part; counted for a full batch)
+  const int agg = (c->k.num_paths == 8 ? (use_sweep(c) ? 1 : 3) : 1) + 2;
   int parts = 1;
   if (use_sweep(c) && sweep_part(c, c->nb) > 0) {
     const int m = sweep_part(c, c->nb);
     parts = (c->nb + m - 1) / m;
   }
-  return per * parts + (c->k.band ? 1 : 0);   // + band clamp
+  return front_launches(c->k) + agg * parts + (c->k.band ? 1 : 0);   // + band clamp
 }
 
 // an event of the pool (null when none can be created: that launch goes untimed)
@@ -507,7 +506,8 @@ static sgmf_status front_stages(sgmf_ctx *c, int f0, int nf, const uint8_t *left
     // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end; the
     // row-pass results of frames [f0, f0 + nf) in their own part of boxTmp
     TIMED(c, "boxor", s, launch_boxor(k, nf, bp.dbar, c->b.boxTmp + (size_t)2 * f0 * k.MW * px,
-                                      k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s));
+                                      k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s,
+                                      bp.gate));
   }
   if (k.semidense) TIMED(c, "semidense", s, launch_semidense(k, bp, nf, s));
   if (cost) TIMED(c, "cost", s, launch_cost(k, bp, nf, s));
@@ -528,30 +528,19 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
   const KParams ka = agg_params(c);
   const int m = ka.sweep ? sweep_part(c, n) : 0;
   if (m > 0) {
-    // Parts of m frames.  Part i: its sweep on the context's stream, then
-    // its row kernel and check on the side stream, while part i + 1's
-    // front stages run on the front stream.  The side and front streams
-    // start after the work enqueued on the context's stream so far; the
-    // context's stream goes on after the last part's check.
-    const int parts = (n + m - 1) / m;
-    CUDA_TRY(c, cudaEventRecord(c->ev_in, s));
-    CUDA_TRY(c, cudaStreamWaitEvent(c->front, c->ev_in, 0));
-    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_in, 0));
-    sgmf_status st = front_stages(c, 0, std::min(m, n), left, right, lidar, true, c->front);
+    // Parts of m frames after the front stages of all n: part i's sweep on
+    // the context's stream, then its row kernel and check on the side
+    // stream while part i + 1 is in the sweep; the context's stream goes on
+    // after the last part's check.  (Running part i + 1's front stages on a
+    // third stream beside part i's sweep was measured and gave nothing: the
+    // sweep keeps the SMs it holds busy, and the front kernels slowed it.)
+    sgmf_status st = front_stages(c, 0, n, left, right, lidar, true, s);
     if (st != SGMF_OK) return st;
-    CUDA_TRY(c, cudaEventRecord(c->ev_front[0], c->front));
-    for (int i = 0; i < parts; ++i) {
-      const int f0 = i * m, nf = std::min(m, n - f0);
+    for (int i = 0, f0 = 0; f0 < n; ++i, f0 += m) {
+      const int nf = std::min(m, n - f0);
       const Buffers bp = frame_view(k, c->b, f0);
-      CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_front[i], 0));
       TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, bp, nf, s));
       CUDA_TRY(c, cudaEventRecord(c->ev_part[i], s));
-      if (i + 1 < parts) {
-        const int f1 = f0 + m;
-        st = front_stages(c, f1, std::min(m, n - f1), left, right, lidar, true, c->front);
-        if (st != SGMF_OK) return st;
-        CUDA_TRY(c, cudaEventRecord(c->ev_front[i + 1], c->front));
-      }
       CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part[i], 0));
       TIMED(c, "agg_rows_wta", c->side, launch_agg_rows(ka, bp, nf, c->spill8, c->side));
       TIMED(c, "consistency", c->side, launch_consistency(k, bp, nf, out + f0 * px, c->side));
@@ -893,12 +882,32 @@ extern "C" sgmf_status sgmf_compute_banded_back(sgmf_ctx *c, int n, const int16_
   TIMED(c, "band_clamp", s, launch_band_clamp(k, c->b, n, band_lo, s));
   TIMED(c, "cost", s, launch_cost_banded(k, c->b, n, s));
   const KParams ka = agg_params(c);
-  if (ka.sweep)
-    TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, c->b, n, s));
-  else
-    TIMED(c, "agg_lines", s, launch_agg_lines(ka, c->b, n, c->spill8, s));
-  TIMED(c, "agg_rows_wta", s, launch_agg_rows(ka, c->b, n, c->spill8, s));
-  TIMED(c, "consistency", s, launch_consistency(k, c->b, n, out, s));
+  const int m = ka.sweep ? sweep_part(c, n) : 0;
+  if (m > 0) {
+    // parts of m frames: part i's row kernel and check on the side stream
+    // beside part i + 1's sweep (as in sgmf_compute_batch)
+    const size_t px = (size_t)k.W * k.H;
+    CUDA_TRY(c, cudaEventRecord(c->ev_in, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_in, 0));
+    for (int i = 0, f0 = 0; f0 < n; ++i, f0 += m) {
+      const int nf = std::min(m, n - f0);
+      const Buffers bp = frame_view(k, c->b, f0);
+      TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, bp, nf, s));
+      CUDA_TRY(c, cudaEventRecord(c->ev_part[i], s));
+      CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_part[i], 0));
+      TIMED(c, "agg_rows_wta", c->side, launch_agg_rows(ka, bp, nf, c->spill8, c->side));
+      TIMED(c, "consistency", c->side, launch_consistency(k, bp, nf, out + f0 * px, c->side));
+    }
+    CUDA_TRY(c, cudaEventRecord(c->ev_rows, c->side));
+    CUDA_TRY(c, cudaStreamWaitEvent(s, c->ev_rows, 0));
+  } else {
+    if (ka.sweep)
+      TIMED(c, "agg_sweep", s, launch_agg_sweep(ka, c->b, n, s));
+    else
+      TIMED(c, "agg_lines", s, launch_agg_lines(ka, c->b, n, c->spill8, s));
+    TIMED(c, "agg_rows_wta", s, launch_agg_rows(ka, c->b, n, c->spill8, s));
+    TIMED(c, "consistency", s, launch_consistency(k, c->b, n, out, s));
+  }
   c->computed = true;
   c->last_n = n;
   c->front_n = 0;

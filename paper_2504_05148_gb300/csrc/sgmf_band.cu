@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) k_cost_banded(KParams k, Buffers b0, cons
   __shared__ uint8_t tab_s[4 * 64];
   __shared__ __align__(16) uint8_t out_s[kBandCostPx * B];
   const Buffers b = frame_view(k, b0, blockIdx.z);
+  if (gated_off(b.gate, k.gate_run)) return;
   const int x0 = blockIdx.x * kBandCostPx, y = blockIdx.y, W = k.W;
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;

@@ -586,11 +586,34 @@ __global__ void k_bn_adam(int count, float *__restrict__ w, float *__restrict__ 
   if (wb) wb[i] = f2bf(wi);
 }
 
+// ---- training batches and weight copies ----------------------------------------------------
+// dst row i = src row idx[i] (rows of row_vec elements of type T, 16 or 4
+// bytes): a training batch gathered from the resident training set; an
+// index outside [0, rows) leaves its destination row untouched
+template <typename T>
+__global__ void __launch_bounds__(256) k_bn_gather(int n, const int *__restrict__ idx, long long rows, long long row_vec,
+                                                   const T *__restrict__ src, T *__restrict__ dst) {
+  const int i = blockIdx.y;
+  const int r = idx[i];
+  if (r < 0 || (long long)r >= rows) return;
+  const T *s = src + (long long)r * row_vec;
+  T *d = dst + (long long)i * row_vec;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < row_vec; j += (long long)gridDim.x * blockDim.x)
+    d[j] = s[j];
+}
+
+// bf16 copy (round to nearest, ties to even) of count f32 values
+__global__ void __launch_bounds__(256) k_bn_to_bf16(int count, const float *__restrict__ w, uint16_t *__restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) wb[i] = f2bf(w[i]);
+}
+
 // ---- network output -> band starts per tile ----------------------------------------------
 // For each tile (kBandTile / 4 quarter pixels a side): the union [lo_u, hi_u] of the pixels'
 // bands [c - w, c + w]; band start lo = round((lo_u + hi_u) / 2) - B / 2,
 // clamped to [0, D - B].  A tile is uncertain when the smallest confidence in
-// it is below conf_min or the union is wider than B; *uncertain counts them.
+// it is below conf_min or the union is wider than B; uncertain[f] counts the
+// uncertain tiles of frame f.
 __global__ void k_bn_tiles(int n, int W, int H, int D, int B, float conf_min, const float *__restrict__ out,
                            int16_t *__restrict__ lo_tiles, int *uncertain) {
   constexpr int Q = kBandTile / 4;   // quarter pixels per tile side
@@ -616,7 +639,19 @@ __global__ void k_bn_tiles(int n, int W, int H, int D, int B, float conf_min, co
     }
   const int mid = __float2int_rn(0.5f * (lo_u + hi_u));
   lo_tiles[i] = (int16_t)min(max(mid - B / 2, 0), D - B);
-  if (qmin < conf_min || hi_u - lo_u > (float)B) atomicAdd(uncertain, 1);
+  if (qmin < conf_min || hi_u - lo_u > (float)B) atomicAdd(uncertain + f, 1);
+}
+
+// per frame: gate[f] = value when frame f has at most max_tiles uncertain
+// tiles, else `otherwise` (or the gate word is kept when otherwise < 0)
+__global__ void k_bn_decide(int n, int max_tiles, const int *__restrict__ uncertain, int value, int otherwise,
+                            int *__restrict__ gate) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  if (uncertain[f] <= max_tiles)
+    gate[f] = value;
+  else if (otherwise >= 0)
+    gate[f] = otherwise;
 }
 
 }  // namespace sgmf
@@ -733,4 +768,39 @@ extern "C" sgmf_status sgmf_bn_tiles(int n, int width, int height, int max_disp,
   k_bn_tiles<<<(unsigned)((NT + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       n, width, height, max_disp, band, conf_min, out, lo_tiles, uncertain);
   return bn_launch(cudaGetLastError(), "sgmf_bn_tiles");
+}
+
+extern "C" sgmf_status sgmf_bn_decide(int n, int tiles, float max_frac, const int *uncertain, int value,
+                                      int otherwise, int *gate, void *stream) {
+  if (n < 1 || tiles < 1 || !(max_frac >= 0.0f) || !uncertain || !gate) return SGMF_ERR_ARG;
+  const int max_tiles = (int)std::min<double>((double)max_frac * tiles, (double)tiles);
+  k_bn_decide<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(n, max_tiles, uncertain, value,
+                                                                                 otherwise, gate);
+  return bn_launch(cudaGetLastError(), "sgmf_bn_decide");
+}
+
+extern "C" sgmf_status sgmf_bn_gather(int n, const int *idx, long long rows, long long row_bytes, const void *src,
+                                      void *dst, void *stream) {
+  if (n < 1 || n > 65535 || rows < 1 || row_bytes < 4 || row_bytes % 4 != 0 || !idx || !src || !dst ||
+      reinterpret_cast<uintptr_t>(src) % 4 != 0 || reinterpret_cast<uintptr_t>(dst) % 4 != 0)
+    return SGMF_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // 16-byte elements when every row starts on a 16-byte boundary, else words
+  const bool v16 = row_bytes % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(dst) % 16 == 0;
+  const long long vec = row_bytes / (v16 ? 16 : 4);
+  const unsigned bx = (unsigned)std::min<long long>((vec + 255) / 256, 64);
+  if (v16)
+    k_bn_gather<uint4><<<dim3(bx, (unsigned)n), 256, 0, s>>>(n, idx, rows, vec, static_cast<const uint4 *>(src),
+                                                             static_cast<uint4 *>(dst));
+  else
+    k_bn_gather<uint32_t><<<dim3(bx, (unsigned)n), 256, 0, s>>>(n, idx, rows, vec, static_cast<const uint32_t *>(src),
+                                                                static_cast<uint32_t *>(dst));
+  return bn_launch(cudaGetLastError(), "sgmf_bn_gather");
+}
+
+extern "C" sgmf_status sgmf_bn_to_bf16(int count, const float *w, uint16_t *w_bf16, void *stream) {
+  if (count < 1 || !w || !w_bf16) return SGMF_ERR_ARG;
+  k_bn_to_bf16<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(count, w, w_bf16);
+  return bn_launch(cudaGetLastError(), "sgmf_bn_to_bf16");
 }

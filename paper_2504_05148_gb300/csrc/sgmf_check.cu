@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(256) k_consistency(KParams k, Buffers b0, int1
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= k.W || y >= k.H) return;
   const Buffers b = frame_view(k, b0, blockIdx.z);
+  if (gated_off(b.gate, k.gate_run)) return;
   out += (size_t)blockIdx.z * frame_px(k);
   const size_t p = (size_t)y * k.W + x;
   const int ds = b.dstar[p];

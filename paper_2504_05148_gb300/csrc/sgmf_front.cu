@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b0, const uin
   if (x >= k.W || y >= k.H) return;
   const int f = blockIdx.z;
   const Buffers b = frame_view(k, b0, f);
+  if (gated_off(b.gate, k.gate_run)) return;
   const size_t fo = (size_t)f * frame_px(k);
   left += fo;
   right += fo;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, int zoff,
                                                 const __grid_constant__ CUtensorMap mapR) {
   const int f = blockIdx.z;
   const Buffers b = frame_view(k, b0, f);
+  if (gated_off(b.gate, k.gate_run)) return;
   // each box starts on a 128-byte boundary, as cp.async.bulk.tensor requires
   constexpr int kBoxBytes = (kCenBoxH * kCenBoxW + 127) / 128 * 128;
   __shared__ alignas(128) uint8_t tiles[2 * kBoxBytes];
@@ -203,11 +205,12 @@ int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch
 template <int MW>
 __global__ void __launch_bounds__(256) k_boxor_rows(const int16_t *__restrict__ disp, uint32_t *__restrict__ tmpS,
                                                    uint32_t *__restrict__ tmpC, int W, int H, int D, int rs,
-                                                   int rc) {
+                                                   int rc, const int *gate, int run) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int y = blockIdx.y * 8 + warp;
   if (y >= H) return;                          // warps are independent: no block barrier
   const int f = blockIdx.z;
+  if (gated_off(gate ? gate + f : nullptr, run)) return;
   const int x0 = blockIdx.x * 32, x = x0 + lane;
   const int16_t *row = disp + ((size_t)f * H + y) * W;
   const int R = max(rs, rc);                   // an unwanted radius is -1: no pixel is that close
@@ -269,10 +272,11 @@ __host__ __device__ constexpr int boxor_col_smem(int r) { return 2 * (2 * r + 1)
 
 __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
                                                   uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
-                                                  int H, int MW, int rs, int rc, int seg) {
+                                                  int H, int MW, int rs, int rc, int seg, const int *gate, int run) {
   extern __shared__ uint32_t colbuf[];         // [2][L][32]: the two blocks, one word per lane
   const int lane = threadIdx.x;
   const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
+  if (gated_off(gate ? gate + f : nullptr, run)) return;
   const uint32_t *src = which ? tmpC : tmpS;
   uint32_t *dst = which ? boxC : boxS;
   const int r = which ? rc : rs;
@@ -336,22 +340,22 @@ __global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ 
 
 template <int MW>
 static void launch_boxor_rows(const KParams &k, int nf, const int16_t *disp, uint32_t *tS, uint32_t *tC, int rs,
-                              int rc, cudaStream_t s) {
+                              int rc, cudaStream_t s, const int *gate) {
   dim3 g((k.W + 31) / 32, (k.H + 7) / 8, nf);
-  k_boxor_rows<MW><<<g, 256, 0, s>>>(disp, tS, tC, k.W, k.H, k.D, rs, rc);
+  k_boxor_rows<MW><<<g, 256, 0, s>>>(disp, tS, tC, k.W, k.H, k.D, rs, rc, gate, k.gate_run);
 }
 
 cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
-                         uint32_t *boxC, cudaStream_t s) {
+                         uint32_t *boxC, cudaStream_t s, const int *gate) {
   const int rs = boxS != nullptr ? k.rs : -1, rc = boxC != nullptr ? k.rc : -1;
   if (rs < 0 && rc < 0) return cudaSuccess;
   // the row results: S then C (C alone at tmp when S is not wanted)
   uint32_t *tS = tmp, *tC = rs >= 0 ? tmp + (size_t)nf * k.MW * k.W * k.H : tmp;
   switch (k.MW) {
-    case 2: launch_boxor_rows<2>(k, nf, disp, tS, tC, rs, rc, s); break;
-    case 4: launch_boxor_rows<4>(k, nf, disp, tS, tC, rs, rc, s); break;
-    case 6: launch_boxor_rows<6>(k, nf, disp, tS, tC, rs, rc, s); break;
-    case 8: launch_boxor_rows<8>(k, nf, disp, tS, tC, rs, rc, s); break;
+    case 2: launch_boxor_rows<2>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
+    case 4: launch_boxor_rows<4>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
+    case 6: launch_boxor_rows<6>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
+    case 8: launch_boxor_rows<8>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
@@ -370,7 +374,8 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
   while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms) seg /= 2;
   // y: row segment x radius (bit 0), z: frame x word plane
   dim3 g((k.W + 31) / 32, 2 * ((k.H + seg - 1) / seg), nf * k.MW);
-  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc, seg);
+  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc, seg, gate,
+                                                           k.gate_run);
   return cudaGetLastError();
 }
 
@@ -386,6 +391,7 @@ __global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b0) {
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= k.W || y >= k.H) return;
   const Buffers b = frame_view(k, b0, blockIdx.z);
+  if (gated_off(b.gate, k.gate_run)) return;
   const size_t p = (size_t)y * k.W + x;
   const size_t plane = (size_t)k.W * k.H;
   const CT *cl = static_cast<const CT *>(b.censL);
@@ -453,6 +459,7 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
   __shared__ uint8_t tab_s[4 * 64];
   __shared__ __align__(16) uint8_t out_s[PX * Dp];   // the block's cost rows, [x][d]
   const Buffers b = frame_view(k, b0, blockIdx.z);
+  if (gated_off(b.gate, k.gate_run)) return;
   const int x0 = blockIdx.x * PX, y = blockIdx.y, W = k.W;
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;

@@ -47,6 +47,7 @@ struct KParams {
   int band;                   // banded mode: band width B (= Dp); 0 = the plain method
   int tw, th;                 // banded mode: band tiles per row / column
   uint32_t wait_census;       // poll limit of the census kernel's TMA wait (kWaitLimit by default)
+  int gate_run;               // with Buffers::gate: a frame runs when its gate word equals this
 };
 
 struct Buffers {   // base pointers of frame 0
@@ -62,6 +63,7 @@ struct Buffers {   // base pointers of frame 0
   uint16_t *dbg_sum;          // [H][W][Dp] or null
   int *err;                   // device error word
   int16_t *band_lo;           // banded mode: band start per tile, [frame][th][tw] (clamped copy)
+  const int *gate;            // per-frame gate words (caller's device memory) or null: every frame runs
 };
 
 // per-frame element counts
@@ -90,7 +92,15 @@ __host__ __device__ __forceinline__ Buffers frame_view(const KParams &k, const B
   v.spill = static_cast<uint8_t *>(b.spill) + f * 4 * cells * 2;
   v.dbg_sum = (b.dbg_sum != nullptr && f == 0) ? b.dbg_sum : nullptr;
   v.band_lo = b.band_lo ? b.band_lo + (size_t)f * k.th * k.tw : nullptr;
+  v.gate = b.gate ? b.gate + f : nullptr;
   return v;
+}
+
+// Whether the kernels skip a frame: its gate word (gate_f, the frame's own,
+// or null) differs from the context's run value.  Every CTA works on one
+// frame, so the test is uniform per CTA and comes before any barrier or copy.
+__host__ __device__ __forceinline__ bool gated_off(const int *gate_f, int run) {
+  return gate_f != nullptr && *gate_f != run;
 }
 
 // ---- small device helpers ------------------------------------------------
@@ -249,7 +259,7 @@ cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, int zoff, 
 // [0, D) present): radius k.rs into boxS and k.rc into boxC, either may be
 // null; tmp holds nf * MW * H * W words per wanted radius
 cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
-                         uint32_t *boxC, cudaStream_t s);
+                         uint32_t *boxC, cudaStream_t s, const int *gate = nullptr);
 cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);

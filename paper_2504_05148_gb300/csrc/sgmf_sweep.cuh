@@ -47,6 +47,7 @@ struct SweepArgs {
   int strip;              // pixels per CTA (= 2 * warps * P)
   const int16_t *lo;      // banded mode: band starts per tile, [frame][th][tw]; null otherwise
   int tw, th;
+  const int *gate;        // per-frame gate words of the launch's frames, or null
 };
 
 template <int CPL, bool BANDED>
@@ -142,6 +143,8 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
   const int rank = blockIdx.x, ncta = gridDim.x;   // the cluster spans grid.x
   const bool up = blockIdx.y != 0;
   const int f = blockIdx.z;
+  // a skipped frame: every CTA of the cluster (one frame) returns before any copy or barrier
+  if (gated_off(a.gate ? a.gate + f : nullptr, a.k.gate_run)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 4, lig = lane & 15;
   const int nwarp = blockDim.x >> 5, ng = 2 * nwarp, gi = warp * 2 + grp;
   const int x_cta = rank * strip;
@@ -554,6 +557,7 @@ static cudaError_t launch_sweep_b(const KParams &k, const Buffers &b, int nf, cu
   a.sum[0] = b.part[0];
   a.sum[1] = b.part[1];
   a.err = b.err;
+  a.gate = b.gate;
   a.sc.p1x2 = (uint32_t)k.p1 * 0x10001u;
   a.sc.dpx2 = (uint32_t)(k.p2 - k.p1) * 0x10001u;
   a.strip = 2 * warps * CF::P;

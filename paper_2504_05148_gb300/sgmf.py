@@ -43,7 +43,7 @@ EXPORTS = (
     "sgmf_create_banded", "sgmf_compute_banded", "sgmf_band_width", "sgmf_compute_host_batch_async",
     "sgmf_compute_front", "sgmf_prior_device", "sgmf_compute_banded_back",
     "sgmf_bn_pack", "sgmf_bn_conv", "sgmf_bn_wgrad", "sgmf_bn_input", "sgmf_bn_labels", "sgmf_bn_loss",
-    "sgmf_bn_adam", "sgmf_bn_tiles",
+    "sgmf_bn_adam", "sgmf_bn_tiles", "sgmf_bn_gather", "sgmf_bn_to_bf16", "sgmf_bn_decide", "sgmf_set_gate",
 )
 
 
@@ -195,6 +195,10 @@ def lib(path: str | None = None):
         "sgmf_bn_adam": (i, [i, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i, P,
                              P]),
         "sgmf_bn_tiles": (i, [i, i, i, i, i, ctypes.c_float, P, P, P, P]),
+        "sgmf_bn_gather": (i, [i, P, ctypes.c_longlong, ctypes.c_longlong, P, P, P]),
+        "sgmf_bn_to_bf16": (i, [i, P, P, P]),
+        "sgmf_bn_decide": (i, [i, i, ctypes.c_float, P, i, i, P, P]),
+        "sgmf_set_gate": (i, [P, P, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -412,6 +416,25 @@ def sgmf_bn_tiles(n: int, width: int, height: int, max_disp: int, band: int, con
                   lo_tiles: int, uncertain: int, stream: int | None = None) -> None:
     _check(lib().sgmf_bn_tiles(n, width, height, max_disp, band, conf_min, out, lo_tiles, uncertain,
                                stream or None), None)
+
+
+def sgmf_bn_gather(n: int, idx: int, rows: int, row_bytes: int, src: int, dst: int, stream: int | None = None) -> None:
+    """dst row i = src row idx[i] (device pointers; idx int32 on the device)."""
+    _check(lib().sgmf_bn_gather(n, idx, rows, row_bytes, src, dst, stream or None), None)
+
+
+def sgmf_bn_to_bf16(count: int, w: int, w_bf16: int, stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_to_bf16(count, w, w_bf16, stream or None), None)
+
+
+def sgmf_bn_decide(n: int, tiles: int, max_frac: float, uncertain: int, value: int, otherwise: int, gate: int,
+                   stream: int | None = None) -> None:
+    _check(lib().sgmf_bn_decide(n, tiles, max_frac, uncertain, value, otherwise, gate, stream or None), None)
+
+
+def sgmf_set_gate(ctx: int, gate: int | None, run: int = 0) -> None:
+    """Per-frame gating of the context's kernels (gate: device int pointer or None)."""
+    _check(lib().sgmf_set_gate(ctx, gate or None, run), ctx)
 
 
 def sgmf_set_tuning(ctx: int, line_warps: int, cost_px: int, sweep: int = 0, parts: int = 1) -> None:

@@ -193,11 +193,11 @@ def test_input_labels_loss_tiles_adam(gpu):
     B, qmin = 64, 0.5
     T = S.BAND_TILE
     lo_t = torch.empty((n, (H + T - 1) // T, (W + T - 1) // T), dtype=torch.int16, device="cuda")
-    unc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    unc = torch.zeros(n, dtype=torch.int32, device="cuda")           # one count per frame
     S.sgmf_bn_tiles(n, W, H, D, B, qmin, _dev(out).data_ptr(), lo_t.data_ptr(), unc.data_ptr())
     c, wv, q = N.heads(out.astype(np.float64), D)
     got = lo_t.cpu().numpy()
-    nunc = 0
+    nunc = np.zeros(n, np.int64)
     for f in range(n):
         for ty in range(got.shape[1]):
             for tx in range(got.shape[2]):
@@ -206,8 +206,16 @@ def test_input_labels_loss_tiles_adam(gpu):
                 lo_u, hi_u = (c[sl] - wv[sl]).min(), (c[sl] + wv[sl]).max()
                 mid = np.rint(0.5 * (lo_u + hi_u))
                 assert abs(int(got[f, ty, tx]) - int(np.clip(mid - B // 2, 0, D - B))) <= 1
-                nunc += bool(q[sl].min() < qmin or hi_u - lo_u > B)
-    assert abs(int(unc.item()) - nunc) <= 1
+                nunc[f] += bool(q[sl].min() < qmin or hi_u - lo_u > B)
+    assert np.abs(unc.cpu().numpy() - nunc).max() <= 1
+    # the per-frame choice: value where the count is at most frac * tiles, else otherwise / kept
+    tiles = got.shape[1] * got.shape[2]
+    cnt_f = unc.cpu().numpy().astype(np.int64)
+    gate = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    for frac, value, other in ((0.5, 1, 2), (0.1, 0, -1)):
+        S.sgmf_bn_decide(n, tiles, frac, unc.data_ptr(), value, other, gate.data_ptr())
+    want = np.where(cnt_f <= int(0.1 * tiles), 0, np.where(cnt_f <= int(0.5 * tiles), 1, 2))
+    np.testing.assert_array_equal(gate.cpu().numpy(), want)
     # Adam
     cnt_p = 1000
     wv0 = rng.normal(size=cnt_p).astype(np.float32)

@@ -75,15 +75,17 @@ def test_training_lowers_the_loss(gpu, trained):
 
 
 def _run_learned(net, s, band, conf_min=0.0, fallback_frac=1.0):
+    """One frame through the learned pipeline: (output, band starts, fell back to the plain method)."""
     import torch
     dev = torch.device("cuda")
     L = bandnet.LearnedSGM(s.W, s.H, s.D, net, band=band, conf_min=conf_min, fallback_frac=fallback_frac)
     try:
         out = torch.empty((1, s.H, s.W), dtype=torch.int16, device=dev)
-        fell = L.compute(torch.from_numpy(s.left[None]).to(dev), torch.from_numpy(s.right[None]).to(dev),
-                         torch.from_numpy(s.lidar[None]).to(dev), out)
+        L.compute(torch.from_numpy(s.left[None]).to(dev), torch.from_numpy(s.right[None]).to(dev),
+                  torch.from_numpy(s.lidar[None]).to(dev), out)
         L.sync()
-        return out[0].cpu().numpy(), L.lo[0].cpu().numpy(), fell, dict(L.stats)
+        gate, _ = L.decision()
+        return out[0].cpu().numpy(), L.lo[0][0].cpu().numpy(), bool(gate[0] == L.PLAIN), None
     finally:
         L.close()
 
@@ -112,6 +114,78 @@ def test_training_is_what_makes_the_bands_useful(gpu, trained):
 def test_fallback_runs_the_plain_method(gpu, trained):
     net, _ = trained
     s = scenes.street(930000, 320, 96, 128)
-    got, _, fell, st = _run_learned(net, s, 64, conf_min=1.1, fallback_frac=0.0)   # every tile uncertain
-    assert fell and st["fallback_frames"] == 1
+    got, _, fell, _ = _run_learned(net, s, 64, conf_min=1.1, fallback_frac=0.0)   # every tile uncertain
+    assert fell
     np.testing.assert_array_equal(got, oracle.compute(s.left, s.right, s.lidar, s.D, dumps=False).out)
+
+
+def test_gates_split_a_batch_between_contexts(gpu):
+    """Per-frame gates: one batch, a banded and a plain context sharing it by
+    a device gate array (hand-set here, as sgmf_bn_decide would write it).
+    Each frame's output is exactly the method its gate word names, and a
+    context leaves the frames it skips untouched."""
+    import torch
+    dev = torch.device("cuda")
+    frames = [scenes.street(940000 + i, 320, 96, 128) for i in range(4)]
+    st = lambda k: torch.from_numpy(np.stack([getattr(f, k) for f in frames])).to(dev)
+    gate_h = np.array([0, 1, 1, 0], np.int32)
+    gate = torch.from_numpy(gate_h).to(dev)
+    th, tw = (96 + S.BAND_TILE - 1) // S.BAND_TILE, (320 + S.BAND_TILE - 1) // S.BAND_TILE
+    rng = np.random.default_rng(3)
+    lo = rng.integers(0, 128 - 64 + 1, size=(4, th, tw)).astype(np.int16)
+    banded = S.Context(320, 96, 128, band=64, max_batch=4)
+    plain = S.Context(320, 96, 128, max_batch=4)
+    try:
+        out = torch.full((4, 96, 320), 7777, dtype=torch.int16, device=dev)
+        S.sgmf_set_gate(banded.handle, gate.data_ptr(), 0)
+        banded.compute_banded(st("left"), st("right"), st("lidar"), torch.from_numpy(lo).to(dev), out)
+        banded.sync()
+        only_banded = out.cpu().numpy().copy()
+        S.sgmf_set_gate(plain.handle, gate.data_ptr(), 1)
+        plain.compute(st("left"), st("right"), st("lidar"), out)
+        plain.sync()
+        got = out.cpu().numpy()
+    finally:
+        banded.close()
+        plain.close()
+    for i, f in enumerate(frames):
+        if gate_h[i] == 1:
+            assert (only_banded[i] == 7777).all(), "the banded context wrote a frame it skips"
+            want = oracle.compute(f.left, f.right, f.lidar, f.D, dumps=False).out
+        else:
+            want = oracle.compute_banded(f.left, f.right, f.lidar, f.D, 64,
+                                         oracle.expand_tiles(lo[i], f.W, f.H, S.BAND_TILE)).out
+        np.testing.assert_array_equal(got[i], want, err_msg=f"frame {i}, gate {gate_h[i]}")
+
+
+def test_learned_batch_frames_follow_their_decision(gpu, trained):
+    """Two band widths in one learned call: every frame's output equals the
+    banded oracle on the bands of the width its device-side decision chose
+    (or the plain method where it fell back)."""
+    import torch
+    net, _ = trained
+    dev = torch.device("cuda")
+    frames = [scenes.street(941000 + i, 320, 96, 128) for i in range(3)]
+    st = lambda k: torch.from_numpy(np.stack([getattr(f, k) for f in frames])).to(dev)
+    L = bandnet.LearnedSGM(320, 96, 128, net, bands=(64, 128), conf_min=0.5, fallback_frac=0.5, max_batch=3)
+    try:
+        out = torch.empty((3, 96, 320), dtype=torch.int16, device=dev)
+        L.compute(st("left"), st("right"), st("lidar"), out)
+        L.sync()
+        gate, unc = L.decision()
+        got = out.cpu().numpy()
+        los = [t.cpu().numpy() for t in L.lo]
+    finally:
+        L.close()
+    tiles = L.th * L.tw
+    for i, f in enumerate(frames):
+        g = int(gate[i])
+        want_g = 0 if unc[0, i] <= int(0.5 * tiles) else (1 if unc[1, i] <= int(0.5 * tiles) else L.PLAIN)
+        assert g == want_g, (i, gate, unc)
+        if g == L.PLAIN:
+            want = oracle.compute(f.left, f.right, f.lidar, f.D, dumps=False).out
+        else:
+            B = L.bands[g]
+            want = oracle.compute_banded(f.left, f.right, f.lidar, f.D, B,
+                                         oracle.expand_tiles(los[g][i], f.W, f.H, S.BAND_TILE)).out
+        np.testing.assert_array_equal(got[i], want, err_msg=f"frame {i}, path {g}")
