@@ -403,8 +403,9 @@ sgmf_status sgmf_set_gate(sgmf_ctx *c, const int *gate, int run);
 typedef struct {
     int32_t line_warps;   /* warps per CTA of the vertical/diagonal line kernels
                              (each warp walks two lines): 1, 2, 4 (default) or 8 */
-    int32_t cost_px;      /* pixels of one row per CTA of the cost kernel: 32, 64 or
-                             128 (default) */
+    int32_t cost_px;      /* the cost kernel takes row segments of at most
+                             8 x cost_px pixels per CTA: 32, 64 or 128 (default;
+                             segments of up to 1024 pixels) */
     int32_t sweep;        /* 1: the six vertical and diagonal directions run as two
                              row-synchronous sweeps of a thread-block cluster per
                              frame (one launch) instead of the three line kernels

@@ -427,9 +427,9 @@ static KParams agg_params(const sgmf_ctx *c) {
   return k;
 }
 
-// launches of the front stages (ingest, census, box-OR rows and columns, semidense, cost)
+// launches of the front stages (ingest, census, box-OR rows and columns, cost with Eq. 5 inside)
 static int front_launches(const KParams &k) {
-  return 3 + ((k.semidense || need_boxc(k)) ? 2 : 0) + (k.semidense ? 1 : 0);
+  return 3 + ((k.semidense || need_boxc(k)) ? 2 : 0);
 }
 
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
@@ -442,7 +442,8 @@ extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
     const int m = sweep_part(c, c->nb);
     parts = (c->nb + m - 1) / m;
   }
-  return front_launches(c->k) + agg * parts + (c->k.band ? 1 : 0);   // + band clamp
+  // banded: the front half runs Eq. 5 on its own (+1) and the back half clamps the bands (+1)
+  return front_launches(c->k) + agg * parts + (c->k.band ? 1 + (c->k.semidense ? 1 : 0) : 0);
 }
 
 // an event of the pool (null when none can be created: that launch goes untimed)
@@ -509,7 +510,9 @@ static sgmf_status front_stages(sgmf_ctx *c, int f0, int nf, const uint8_t *left
                                       k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s,
                                       bp.gate));
   }
-  if (k.semidense) TIMED(c, "semidense", s, launch_semidense(k, bp, nf, s));
+  // with the cost volume, Eq. 5 runs inside the cost kernel (its candidates'
+  // right-census words are staged there anyway); alone for the banded front half
+  if (k.semidense && !cost) TIMED(c, "semidense", s, launch_semidense(k, bp, nf, s));
   if (cost) TIMED(c, "cost", s, launch_cost(k, bp, nf, s));
   return SGMF_OK;
 }

@@ -430,68 +430,99 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 }
 
 // --------------------------------------------------------------------------
-// Joint cost C-bar (Eq. 4).  H(p,d) = popcount(cL(x,y) ^ cR(x-d,y)), or the
-// number of census bits where x - d < 0.  Where the prior (d-hat, or d-bar
-// for DSGM) is invalid C-bar = H; otherwise
+// Joint cost C-bar (Eq. 4), with semidensification (Eq. 5) fused in.
+// H(p,d) = popcount(cL(x,y) ^ cR(x-d,y)), or the number of census bits where
+// x - d < 0.  Where the prior (d-hat, or d-bar for DSGM) is invalid C-bar = H;
+// otherwise
 //   C-bar = floor(((b-a) H + a q + floor(b/2)) / b),  q = 0 / q1 / q2 for
 // |d - prior| = 0 / 1 / > 1, looked up in a table built on the host.
-// A CTA handles PX pixels of one row (32, 64 or 128, a tuning choice): their
-// right-census window is staged in shared memory, the lanes of a warp walk
-// the disparities of one pixel, and the CTA's [PX][Dp] cost rows, assembled
-// in shared memory, leave as 16-byte stores (cells d >= D hold 0).
-
-
-
-// A lane owns DPL consecutive disparities d0 = DPL * lane .. d0 + DPL - 1 of
-// a pixel, whose right-census words cR(x - d) are DPL consecutive entries of
-// the staged window.  They are read as aligned vectors (CostVec): the window
-// is staged VL times, copy k shifted by k entries, and a pixel reads the copy
-// that puts its run on a vector boundary (lanes DPL entries apart: one vector
-// per lane, no bank conflicts).  The lane packs its cost bytes into words.
-template <typename CT, int DPL, int PX>
-__global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __grid_constant__ CostTable tab) {
+//
+// A CTA takes a segment of one row (up to 8 x cost_px pixels, a tuning
+// choice: 256, 512 or 1024) and stages the right-census window of the
+// segment in shared memory once: VL copies, copy k shifted by k entries, so
+// that a lane reads its DPL consecutive entries cR(x - d) as aligned vectors
+// (lanes DPL entries apart: one vector per lane, no bank conflicts).  Then
+// (1) one thread per pixel computes d-hat of Eq. 5 from the box-ORed mask of
+// its r_s window: the candidates are the mask's set bits, each H taken from
+// the staged window, visited in increasing d so that the first strict
+// minimum is the lexicographic (H, d) minimum; d-hat = that d if min H < T_s,
+// else d-bar; (2) the lanes of a warp take the disparities of one pixel at a
+// time and store its Dp cost bytes directly: one 4- to 16-byte store a lane,
+// a warp's stores one contiguous row of the cost volume.
+template <typename CT, int DPL, bool SEMI>
+__global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const __grid_constant__ CostTable tab,
+                                                  int seg, int nwin) {
   constexpr int Dp = 32 * DPL;
   using CV = CostVec<CT, DPL>;
-  constexpr int VL = CV::VL, NV = DPL / VL, NW = PX + Dp;
-  __shared__ __align__(16) CT cr_s[VL][NW];      // copy k: cr_s[k][i] = cR(base + i + k)
-  __shared__ CT cl_s[PX];
-  __shared__ int pd_s[PX];
-  __shared__ uint8_t tab_s[4 * 64];
-  __shared__ __align__(16) uint8_t out_s[PX * Dp];   // the block's cost rows, [x][d]
+  constexpr int VL = CV::VL, NV = DPL / VL;
+  extern __shared__ __align__(16) uint8_t cs_smem[];
+  CT *cr_s = reinterpret_cast<CT *>(cs_smem);                 // [VL][nwin]: copy k, cr_s[k][i] = cR(base + i + k)
+  CT *cl_s = cr_s + (size_t)VL * nwin;                        // [seg]
+  int *pd_s = reinterpret_cast<int *>(cl_s + seg);            // [seg] the prior of each pixel
+  uint8_t *tab_s = reinterpret_cast<uint8_t *>(pd_s + seg);  // [4][64]
   const Buffers b = frame_view(k, b0, blockIdx.z);
   if (gated_off(b.gate, k.gate_run)) return;
-  const int x0 = blockIdx.x * PX, y = blockIdx.y, W = k.W;
+  const int x0 = blockIdx.x * seg, y = blockIdx.y, W = k.W;
+  const int npx = min(seg, W - x0);
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
-  const int16_t *prior = (k.semidense ? b.dhat : b.dbar) + rowp;
   const int base = x0 - (Dp - 1);
+  const int nw = npx + Dp;                                   // staged entries of one copy
 #pragma unroll
   for (int kk = 0; kk < VL; ++kk)
-    for (int j = threadIdx.x; j < NW; j += blockDim.x) {
+    for (int j = threadIdx.x; j < nw; j += blockDim.x) {
       const int xx = base + j + kk;
-      cr_s[kk][j] = (j + kk < PX + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
+      cr_s[kk * nwin + j] = (j + kk < npx + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
     }
-  if (threadIdx.x < PX) {
-    const int xx = x0 + threadIdx.x;
-    const int pd = xx < W ? prior[xx] : -1;
-    cl_s[threadIdx.x] = xx < W ? cl[xx] : (CT)0;
-    pd_s[threadIdx.x] = pd;
-  }
+  for (int i = threadIdx.x; i < npx; i += blockDim.x) cl_s[i] = cl[x0 + i];
   for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // (1) the prior of every pixel of the segment
+  const size_t plane = (size_t)W * k.H;
+  for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+    const size_t p = rowp + x0 + i;
+    const int db = b.dbar[p];
+    int pd = db;
+    if (SEMI) {
+      const int x = x0 + i;
+      const CT c = cl_s[i];
+      uint32_t mw[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) mw[w] = w < k.MW ? b.boxS[w * plane + p] : 0u;
+      int best_h = 0x7fffffff, best_d = -1;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        if (w >= k.MW || best_h == 0) break;
+        uint32_t m = mw[w];
+        while (m != 0u) {
+          const int d = w * 32 + __ffs(m) - 1;
+          m &= m - 1u;
+          const int h = x >= d ? hamming<CT>(c, cr_s[i + Dp - 1 - d]) : k.nbits;
+          if (h < best_h) {
+            best_h = h;
+            best_d = d;
+            if (h == 0) break;
+          }
+        }
+      }
+      pd = (best_d >= 0 && best_h < k.ts) ? best_d : db;
+      b.dhat[p] = (int16_t)pd;
+    }
+    pd_s[i] = pd;
+  }
+  __syncthreads();
+  // (2) the cost bytes, one pixel per warp at a time
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int d0 = DPL * lane;
-  const int npx = min(PX, W - x0);
-  // every d of every pixel has x - d >= 0 and every cell is a real disparity
-  const bool inner = x0 >= Dp - 1 && k.D == Dp;
-  for (int px = warp; px < npx; px += 8) {
+  uint8_t *out = b.cost + (rowp + x0) * Dp + d0;
+  for (int px = warp; px < npx; px += nwarp) {
     const int x = x0 + px;
     const CT c = cl_s[px];
     const int pd = pd_s[px];
-    // cR(x - d) for d = d0 + DPL - 1 - m is entry px + Dp - DPL (lane + 1) + m
+    // cR(x - d) for d = d0 + DPL - 1 - m is entry px + Dp - DPL (lane + 1) + m of the copy that aligns it
     const int kk = px % VL;
-    const CT *run = &cr_s[kk][px + Dp - DPL * (lane + 1) - kk];
+    const CT *run = cr_s + kk * nwin + (px + Dp - DPL * (lane + 1) - kk);
     CT v[DPL];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -500,15 +531,24 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
 #pragma unroll
       for (int m = 0; m < VL; ++m) v[q * VL + m] = e[m];
     }
-    uint32_t out[DPL];
-    if (inner) {
+    uint32_t o[DPL];
+    if (x >= Dp - 1 && k.D == Dp) {
+      // every d has x - d >= 0 and is a real disparity
+      uint32_t h[DPL];
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) out[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
+      for (int i = 0; i < DPL; ++i) o[i] = h[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
       if (pd >= 0) {
-        // the far class for every cell; the (at most three) cells with
-        // |d - prior| <= 1 are rewritten after the loop, one thread per pixel
+        // the far class for every cell, then the (at most three) cells with
+        // |d - prior| <= 1, in the one or two lanes that hold them
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) out[i] = tab_s[2 * 64 + out[i]];
+        for (int i = 0; i < DPL; ++i) o[i] = tab_s[2 * 64 + h[i]];
+        if (pd + 1 >= d0 && pd - 1 < d0 + DPL) {
+#pragma unroll
+          for (int i = 0; i < DPL; ++i) {
+            const int dd = d0 + i - pd;
+            if (dd >= -1 && dd <= 1) o[i] = tab_s[(dd != 0) * 64 + h[i]];
+          }
+        }
       }
     } else {
 #pragma unroll
@@ -516,60 +556,42 @@ __global__ void __launch_bounds__(256) k_cost(KParams k, Buffers b0, const __gri
         const int d = d0 + i;
         const int h = x >= d ? hamming<CT>(c, v[DPL - 1 - i]) : k.nbits;
         const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
-        out[i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
+        o[i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
       }
     }
-    store_cost_bytes<DPL>(out_s + px * Dp + d0, out);
+    store_cost_bytes<DPL>(out + (size_t)px * Dp, o);
   }
-  __syncthreads();
-  if (inner && threadIdx.x < npx) {
-    const int px = threadIdx.x, pd = pd_s[px];
-    if (pd >= 0) {
-      const CT c = cl_s[px];
-#pragma unroll
-      for (int j = -1; j <= 1; ++j) {
-        const int d = pd + j;
-        if (d >= 0 && d < Dp)
-          out_s[px * Dp + d] = tab_s[abs(j) * 64 + hamming<CT>(c, cr_s[0][px + Dp - 1 - d])];
-      }
-    }
-  }
-  __syncthreads();
-  // the block's [npx][Dp] bytes are contiguous in the cost volume: 16-byte stores
-  uint4 *dst = reinterpret_cast<uint4 *>(b.cost + (rowp + x0) * Dp);
-  const uint4 *src = reinterpret_cast<const uint4 *>(out_s);
-  const int nvec = npx * Dp / 16;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
 }
 
-template <typename CT, int PX>
-static void launch_cost_px(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
-  dim3 grid((k.W + PX - 1) / PX, k.H, nf);
+template <typename CT, bool SEMI>
+static cudaError_t launch_cost_t(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
+  // segments of at most 8 x cost_px pixels, equal lengths
+  const int segmax = 8 * k.cost_px;
+  const int nseg = (k.W + segmax - 1) / segmax, seg = (k.W + nseg - 1) / nseg;
+  const int Dp = k.Dp;
+  const int VL = sizeof(CT) == 8 ? 2 : (k.DPL % 4 == 0 ? 4 : 2);
+  const int nwin = (seg + Dp + 3) / 4 * 4;                 // copy length, rows 16-byte aligned
+  const size_t smem = (size_t)VL * nwin * sizeof(CT) + (size_t)seg * sizeof(CT) + (size_t)seg * 4 + 256;
+  dim3 grid(nseg, k.H, nf);
+  // at most 2 x (1024 + 256) u64 entries + the segment's arrays: below the 48 KiB default
+  if (smem > 48 * 1024) return cudaErrorInvalidConfiguration;
+  auto launch = [&](auto kern) -> cudaError_t {
+    kern<<<grid, 256, smem, s>>>(k, b, tab, seg, nwin);
+    return cudaGetLastError();
+  };
   switch (k.DPL) {
-    case 2: k_cost<CT, 2, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
-    case 4: k_cost<CT, 4, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
-    case 6: k_cost<CT, 6, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
-    default: k_cost<CT, 8, PX><<<grid, 256, 0, s>>>(k, b, tab); break;
-  }
-}
-
-// pixels per CTA from the context's tuning (32, 64 or 128)
-template <typename CT>
-static void launch_cost_t(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
-  switch (k.cost_px) {
-    case 32: launch_cost_px<CT, 32>(k, b, nf, tab, s); break;
-    case 64: launch_cost_px<CT, 64>(k, b, nf, tab, s); break;
-    default: launch_cost_px<CT, 128>(k, b, nf, tab, s); break;
+    case 2: return launch(k_cost_seg<CT, 2, SEMI>);
+    case 4: return launch(k_cost_seg<CT, 4, SEMI>);
+    case 6: return launch(k_cost_seg<CT, 6, SEMI>);
+    default: return launch(k_cost_seg<CT, 8, SEMI>);
   }
 }
 
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
   const CostTable tab = cost_table(k);
   if (k.census == 1)
-    launch_cost_t<uint64_t>(k, b, nf, tab, s);
-  else
-    launch_cost_t<uint32_t>(k, b, nf, tab, s);
-  return cudaGetLastError();
+    return k.semidense ? launch_cost_t<uint64_t, true>(k, b, nf, tab, s) : launch_cost_t<uint64_t, false>(k, b, nf, tab, s);
+  return k.semidense ? launch_cost_t<uint32_t, true>(k, b, nf, tab, s) : launch_cost_t<uint32_t, false>(k, b, nf, tab, s);
 }
 
 }  // namespace sgmf

@@ -60,7 +60,7 @@ SHAPES = [(1242, 24, 128), (2040, 6, 128), (1280, 12, 64), (1280, 6, 256), (640,
 def test_sweep_matches_oracle(gpu, W, H, D):
     s = scenes.random_small(W * 7 + H * 3 + D, W, H, D)
     g = _check(s)
-    assert g["launches"] == 9             # one sweep launch instead of three line launches
+    assert g["launches"] == 8             # one sweep launch instead of three line launches
 
 
 @pytest.mark.parametrize("case", ["u16_range", "subpixel", "dsgm", "census_full", "no_check"])
