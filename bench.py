@@ -690,7 +690,7 @@ def run_learned(args, rank, world):
 EXTRAS = {
     "mixed": ["--workload", "mixed", "--steps", "5", "--warmup", "3"],
     "serve": ["--workload", "serve", "--serve-seconds", "3"],
-    "learned": ["--workload", "learned", "--eval-frames", "8", "--learned-batch", "8", "--steps-learned", "2"],
+    "learned": ["--workload", "learned", "--eval-frames", "24", "--learned-batch", "12", "--steps-learned", "2"],
 }
 EXTRA_KEYS = {
     "mixed": ("metric", "value", "unit", "ms_per_step", "frames_per_s", "e2e", "gpu_launches", "clocks", "config"),
