@@ -288,7 +288,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
   A(dalloc(c, reinterpret_cast<uint64_t **>(&c->b.censR), n * 8));
   A(dalloc(c, &c->b.boxS, n * 4 * k.MW));
   A(dalloc(c, &c->b.boxC, n * 4 * k.MW));
-  A(dalloc(c, &c->b.boxTmp, 2 * n * 4 * k.MW));
+  A(dalloc(c, &c->b.boxTmp, n * 4 * k.MW));
   A(dalloc(c, &c->b.cost, nv));
   for (int i = 0; i < 3; ++i) A(dalloc(c, &c->b.part[i], nv * 2));
   c->spill_bytes = 4 * nv * 2;
@@ -427,9 +427,10 @@ static KParams agg_params(const sgmf_ctx *c) {
   return k;
 }
 
-// launches of the front stages (ingest, census, box-OR rows and columns, cost with Eq. 5 inside)
+// launches of the front stages (ingest, census, box-OR row pass and, for
+// Eq. 5, its column pass, cost with Eq. 5 inside)
 static int front_launches(const KParams &k) {
-  return 3 + ((k.semidense || need_boxc(k)) ? 2 : 0);
+  return 3 + ((k.semidense || need_boxc(k)) ? 1 : 0) + (k.semidense ? 1 : 0);
 }
 
 extern "C" int sgmf_launches_per_compute(const sgmf_ctx *c) {
@@ -504,9 +505,10 @@ static sgmf_status front_stages(sgmf_ctx *c, int f0, int nf, const uint8_t *left
   TIMED(c, "ingest", s, launch_ingest(k, bp, nf, left + f0 * px, right + f0 * px, lidar ? lidar + f0 * px : nullptr, s));
   TIMED(c, "census", s, launch_census(k, bp, nf, f0, &c->mapL, &c->mapR, s));
   if (k.semidense || need_boxc(k)) {
-    // both windows at once: r_s for Eq. 5 now, r_c for Eq. 6 at the end; the
-    // row-pass results of frames [f0, f0 + nf) in their own part of boxTmp
-    TIMED(c, "boxor", s, launch_boxor(k, nf, bp.dbar, c->b.boxTmp + (size_t)2 * f0 * k.MW * px,
+    // both windows' row pass at once; the column pass for r_s (Eq. 5) into
+    // boxS, from the row results of frames [f0, f0 + nf) in their own part
+    // of boxTmp; the r_c row ORs (Eq. 6) stay in boxC for the check
+    TIMED(c, "boxor", s, launch_boxor(k, nf, bp.dbar, c->b.boxTmp + (size_t)f0 * k.MW * px,
                                       k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s,
                                       bp.gate));
   }
@@ -534,9 +536,10 @@ extern "C" sgmf_status sgmf_compute_batch(sgmf_ctx *c, int n, const uint8_t *lef
     // Parts of m frames after the front stages of all n: part i's sweep on
     // the context's stream, then its row kernel and check on the side
     // stream while part i + 1 is in the sweep; the context's stream goes on
-    // after the last part's check.  (Running part i + 1's front stages on a
-    // third stream beside part i's sweep was measured and gave nothing: the
-    // sweep keeps the SMs it holds busy, and the front kernels slowed it.)
+    // after the last part's check.  (Running the later parts' front stages
+    // on the side stream beside the first part's sweep was measured twice
+    // and gave nothing: 8.17-8.24 against 8.20 ms for 32 KITTI frames, and
+    // 3 % slower at 64; the sweep slows by what the front stages save.)
     sgmf_status st = front_stages(c, 0, n, left, right, lidar, true, s);
     if (st != SGMF_OK) return st;
     for (int i = 0, f0 = 0; f0 < n; ++i, f0 += m) {
@@ -694,7 +697,12 @@ extern "C" sgmf_status sgmf_debug_stage(sgmf_ctx *c, int stage, void *dst, size_
     case SGMF_STAGE_DPRIME: CUDA_TRY(c, cudaMemcpy(dst, c->b.dprime, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_DSUB: CUDA_TRY(c, cudaMemcpy(dst, c->b.dsub, need, cudaMemcpyDeviceToHost)); break;
     case SGMF_STAGE_BOX_S: CUDA_TRY(c, cudaMemcpy(dst, c->b.boxS, need, cudaMemcpyDeviceToHost)); break;
-    case SGMF_STAGE_BOX_C: CUDA_TRY(c, cudaMemcpy(dst, c->b.boxC, need, cudaMemcpyDeviceToHost)); break;
+    case SGMF_STAGE_BOX_C:
+      // the pipeline keeps the row ORs only: the column pass of frame 0 into scratch
+      LAUNCH_TRY(c, launch_boxor_cols(k, 1, c->b.boxC, c->b.boxTmp, k.rc, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      CUDA_TRY(c, cudaMemcpy(dst, c->b.boxTmp, need, cudaMemcpyDeviceToHost));
+      break;
     case SGMF_STAGE_CENSUS_L:
     case SGMF_STAGE_CENSUS_R: {
       const void *src = stage == SGMF_STAGE_CENSUS_L ? c->b.censL : c->b.censR;

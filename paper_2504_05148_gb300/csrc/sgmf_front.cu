@@ -195,7 +195,9 @@ int make_image_tmap(void *tmap_out, const uint8_t *base, int W, int H, int pitch
 // of bit d & 31 of word d >> 5.  The OR over a clipped square is the OR over
 // its rows of the ORs along each row, so a row pass and a column pass make
 // it exactly.  Both radii (r_s of Eq. 5, r_c of Eq. 6) come out of one row
-// pass and one column launch.
+// pass; the column pass runs for r_s only.  The r_c row ORs stay as they are
+// (in boxC): Eq. 6 needs its LiDAR term only at pixels whose stereo term
+// fails, and the check kernel ORs those pixels' 2 r_c + 1 rows itself.
 //
 // Row pass, from the sparse map itself: a warp owns 32 consecutive pixels of
 // one row and visits the valid pixels of [x0 - R, x0 + 31 + R] (R the larger
@@ -270,19 +272,14 @@ constexpr int kColSeg = 128, kColSegMin = 32, kColChunk = 8;
 
 __host__ __device__ constexpr int boxor_col_smem(int r) { return 2 * (2 * r + 1) * 32 * 4; }
 
-__global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ tmpS, const uint32_t *__restrict__ tmpC,
-                                                  uint32_t *__restrict__ boxS, uint32_t *__restrict__ boxC, int W,
-                                                  int H, int MW, int rs, int rc, int seg, const int *gate, int run) {
+__global__ void __launch_bounds__(32) k_boxor_cols(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                  int W, int H, int MW, int r, int seg, const int *gate, int run) {
   extern __shared__ uint32_t colbuf[];         // [2][L][32]: the two blocks, one word per lane
   const int lane = threadIdx.x;
-  const int f = blockIdx.z / MW, w = blockIdx.z % MW, which = blockIdx.y & 1;
+  const int f = blockIdx.z / MW, w = blockIdx.z % MW;
   if (gated_off(gate ? gate + f : nullptr, run)) return;
-  const uint32_t *src = which ? tmpC : tmpS;
-  uint32_t *dst = which ? boxC : boxS;
-  const int r = which ? rc : rs;
-  if (r < 0) return;                           // this radius is not wanted
   const size_t base = ((size_t)f * MW + w) * H * W;
-  const int x = blockIdx.x * 32 + lane, y0 = (blockIdx.y >> 1) * seg;
+  const int x = blockIdx.x * 32 + lane, y0 = blockIdx.y * seg;
   const int L = 2 * r + 1, T = min(seg, H - y0), n = T + 2 * r, ylo = y0 - r;
   const bool live = x < W;
   // lanes past the image's right edge read its last column and store nothing
@@ -345,12 +342,33 @@ static void launch_boxor_rows(const KParams &k, int nf, const int16_t *disp, uin
   k_boxor_rows<MW><<<g, 256, 0, s>>>(disp, tS, tC, k.W, k.H, k.D, rs, rc, gate, k.gate_run);
 }
 
+// the column pass over nf frames: dst = the (2r+1)-row OR of the row results src
+cudaError_t launch_boxor_cols(const KParams &k, int nf, const uint32_t *src, uint32_t *dst, int r, cudaStream_t s,
+                              const int *gate) {
+  static bool done[64] = {};
+  cudaError_t e = once_per_device(done, [](int) {
+    return cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
+  });
+  int sms = 0;
+  if (e == cudaSuccess) e = sm_count(&sms);
+  if (e != cudaSuccess) return e;
+  // the longest segment whose grid still makes about two waves of one-warp
+  // CTAs (about 20 resident a SM at r = 20)
+  const long ctas_per_seg = (long)((k.W + 31) / 32) * nf * k.MW;
+  int seg = kColSeg;
+  while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms) seg /= 2;
+  // y: row segment, z: frame x word plane
+  dim3 g((k.W + 31) / 32, (k.H + seg - 1) / seg, nf * k.MW);
+  k_boxor_cols<<<g, 32, boxor_col_smem(r), s>>>(src, dst, k.W, k.H, k.MW, r, seg, gate, k.gate_run);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
                          uint32_t *boxC, cudaStream_t s, const int *gate) {
   const int rs = boxS != nullptr ? k.rs : -1, rc = boxC != nullptr ? k.rc : -1;
   if (rs < 0 && rc < 0) return cudaSuccess;
-  // the row results: S then C (C alone at tmp when S is not wanted)
-  uint32_t *tS = tmp, *tC = rs >= 0 ? tmp + (size_t)nf * k.MW * k.W * k.H : tmp;
+  // the row results: r_s into tmp (for the column pass), r_c into boxC itself
+  uint32_t *tS = tmp, *tC = boxC;
   switch (k.MW) {
     case 2: launch_boxor_rows<2>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
     case 4: launch_boxor_rows<4>(k, nf, disp, tS, tC, rs, rc, s, gate); break;
@@ -359,24 +377,8 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  static bool done[64] = {};
-  e = once_per_device(done, [](int) {
-    return cudaFuncSetAttribute(k_boxor_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, boxor_col_smem(255));
-  });
-  int sms = 0;
-  if (e == cudaSuccess) e = sm_count(&sms);
-  if (e != cudaSuccess) return e;
-  // the longest segment whose grid still makes about two waves of one-warp
-  // CTAs (about 20 resident a SM at r = 20)
-  const long ctas_per_seg = (long)((k.W + 31) / 32) * 2 * nf * k.MW;
-  int seg = kColSeg;
-  while (seg > kColSegMin && ctas_per_seg * ((k.H + seg - 1) / seg) < 40L * sms) seg /= 2;
-  // y: row segment x radius (bit 0), z: frame x word plane
-  dim3 g((k.W + 31) / 32, 2 * ((k.H + seg - 1) / seg), nf * k.MW);
-  k_boxor_cols<<<g, 32, boxor_col_smem(max(rs, rc)), s>>>(tS, tC, boxS, boxC, k.W, k.H, k.MW, rs, rc, seg, gate,
-                                                           k.gate_run);
-  return cudaGetLastError();
+  if (e != cudaSuccess || rs < 0) return e;
+  return launch_boxor_cols(k, nf, tS, boxS, rs, s, gate);
 }
 
 // --------------------------------------------------------------------------
@@ -439,48 +441,67 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 //
 // A CTA takes a segment of one row (up to 8 x cost_px pixels, a tuning
 // choice: 256, 512 or 1024) and stages the right-census window of the
-// segment in shared memory once: VL copies, copy k shifted by k entries, so
-// that a lane reads its DPL consecutive entries cR(x - d) as aligned vectors
-// (lanes DPL entries apart: one vector per lane, no bank conflicts).  Then
-// (1) one thread per pixel computes d-hat of Eq. 5 from the box-ORed mask of
-// its r_s window: the candidates are the mask's set bits, each H taken from
-// the staged window, visited in increasing d so that the first strict
-// minimum is the lexicographic (H, d) minimum; d-hat = that d if min H < T_s,
-// else d-bar; (2) the lanes of a warp take the disparities of one pixel at a
-// time and store its Dp cost bytes directly: one 4- to 16-byte store a lane,
-// a warp's stores one contiguous row of the cost volume.
+// segment in shared memory once.  Then (1) one thread per pixel computes
+// d-hat of Eq. 5 from the box-ORed mask of its r_s window: the candidates are
+// the mask's set bits, each H taken from the staged window, visited in
+// increasing d so that the first strict minimum is the lexicographic (H, d)
+// minimum; d-hat = that d if min H < T_s, else d-bar (staging the
+// segment's mask words and d-bar with the census window instead was 13 %
+// slower: the whole CTA then waits on those loads); (2) a warp takes P = 4
+// consecutive pixels at a time,
+// each lane the same DPL disparities of all four: the P + DPL - 1 window
+// entries cR(x - d) they need are consecutive and start on a vector boundary
+// (x - d0 is a multiple of 4 there), so a lane loads them with a few aligned
+// vector loads and indexes them with constants; a lane stores DPL cost bytes
+// a pixel, a warp's stores one contiguous row of the cost volume.  (Eight
+// pixels a step, for fewer loop and load instructions, ran 14 % slower: the
+// registers they need halve the resident warps.)
+constexpr int kCostPix = 4;   // pixels a warp takes at a time
+
+template <typename CT, int DPL>
+struct CostWin {
+  static constexpr int P = kCostPix;
+  static constexpr int VL = sizeof(CT) == 8 ? 2 : (DPL % 4 == 0 ? 4 : 2);   // entries per vector load
+  using V = typename std::conditional<VL * sizeof(CT) == 16, uint4, uint2>::type;
+  static constexpr int NE = (P + DPL - 1 + VL - 1) / VL * VL;             // entries loaded (= P + DPL)
+  static_assert(P % 4 == 0 && DPL % 2 == 0, "aligned window, census and prior loads");
+};
+
 template <typename CT, int DPL, bool SEMI>
 __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const __grid_constant__ CostTable tab,
                                                   int seg, int nwin) {
-  constexpr int Dp = 32 * DPL;
-  using CV = CostVec<CT, DPL>;
-  constexpr int VL = CV::VL, NV = DPL / VL;
+  using CW = CostWin<CT, DPL>;
+  constexpr int Dp = 32 * DPL, P = CW::P;
+  constexpr int VL = CW::VL, NE = CW::NE;
+  __shared__ uint8_t tab_s[4 * 64];                           // fixed address: LDS [h + const]
   extern __shared__ __align__(16) uint8_t cs_smem[];
-  CT *cr_s = reinterpret_cast<CT *>(cs_smem);                 // [VL][nwin]: copy k, cr_s[k][i] = cR(base + i + k)
-  CT *cl_s = cr_s + (size_t)VL * nwin;                        // [seg]
-  int *pd_s = reinterpret_cast<int *>(cl_s + seg);            // [seg] the prior of each pixel
-  uint8_t *tab_s = reinterpret_cast<uint8_t *>(pd_s + seg);  // [4][64]
+  const int segr = (seg + P - 1) / P * P;
+  CT *cr_s = reinterpret_cast<CT *>(cs_smem);                 // [nwin]: cr_s[j] = cR(x0 - (Dp - 1) + j)
+  CT *cl_s = cr_s + nwin;                                     // [segr]
+  int16_t *pd_s = reinterpret_cast<int16_t *>(cl_s + segr);   // the prior of each pixel
   const Buffers b = frame_view(k, b0, blockIdx.z);
   if (gated_off(b.gate, k.gate_run)) return;
   const int x0 = blockIdx.x * seg, y = blockIdx.y, W = k.W;
   const int npx = min(seg, W - x0);
+  const int npr = (npx + P - 1) / P * P;
   const size_t rowp = (size_t)y * W;
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int base = x0 - (Dp - 1);
-  const int nw = npx + Dp;                                   // staged entries of one copy
-#pragma unroll
-  for (int kk = 0; kk < VL; ++kk)
-    for (int j = threadIdx.x; j < nw; j += blockDim.x) {
-      const int xx = base + j + kk;
-      cr_s[kk * nwin + j] = (j + kk < npx + Dp - 1 && xx >= 0 && xx < W) ? cr[xx] : (CT)0;
-    }
-  for (int i = threadIdx.x; i < npx; i += blockDim.x) cl_s[i] = cl[x0 + i];
+  for (int j = threadIdx.x; j < nwin; j += blockDim.x) {
+    const int xx = base + j;
+    cr_s[j] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
+  }
+  for (int i = threadIdx.x; i < npr; i += blockDim.x) cl_s[i] = i < npx ? cl[x0 + i] : (CT)0;
   for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
   // (1) the prior of every pixel of the segment
   const size_t plane = (size_t)W * k.H;
-  for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+  for (int i = threadIdx.x; i < npr; i += blockDim.x) {
+    if (i >= npx) {
+      pd_s[i] = -1;
+      continue;
+    }
     const size_t p = rowp + x0 + i;
     const int db = b.dbar[p];
     int pd = db;
@@ -509,57 +530,86 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
       pd = (best_d >= 0 && best_h < k.ts) ? best_d : db;
       b.dhat[p] = (int16_t)pd;
     }
-    pd_s[i] = pd;
+    pd_s[i] = (int16_t)pd;
   }
   __syncthreads();
-  // (2) the cost bytes, one pixel per warp at a time
+  // (2) the cost bytes, four pixels per warp at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int d0 = DPL * lane;
   uint8_t *out = b.cost + (rowp + x0) * Dp + d0;
-  for (int px = warp; px < npx; px += nwarp) {
-    const int x = x0 + px;
-    const CT c = cl_s[px];
-    const int pd = pd_s[px];
-    // cR(x - d) for d = d0 + DPL - 1 - m is entry px + Dp - DPL (lane + 1) + m of the copy that aligns it
-    const int kk = px % VL;
-    const CT *run = cr_s + kk * nwin + (px + Dp - DPL * (lane + 1) - kk);
-    CT v[DPL];
+  for (int xb = P * warp; xb < npx; xb += P * nwarp) {
+    // cR(x - d) for pixel xb + u and d = d0 + i is entry jlo + DPL - 1 + u - i
+    const int jlo = xb + DPL * (31 - lane);
+    CT e[NE];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const typename CV::V t = reinterpret_cast<const typename CV::V *>(run)[q];
-      const CT *e = reinterpret_cast<const CT *>(&t);
+    for (int q = 0; q < NE / VL; ++q) {
+      const typename CW::V t = reinterpret_cast<const typename CW::V *>(cr_s + jlo)[q];
+      const CT *tv = reinterpret_cast<const CT *>(&t);
 #pragma unroll
-      for (int m = 0; m < VL; ++m) v[q * VL + m] = e[m];
+      for (int m = 0; m < VL; ++m) e[q * VL + m] = tv[m];
     }
-    uint32_t o[DPL];
+    CT c[P];
+    {
+      // 16-byte aligned: xb is a multiple of P
+      constexpr int CV = 16 / sizeof(CT);
+      const uint4 *cv = reinterpret_cast<const uint4 *>(cl_s + xb);
+#pragma unroll
+      for (int q = 0; q < P / CV; ++q) {
+        const uint4 t = cv[q];
+        const CT *tv = reinterpret_cast<const CT *>(&t);
+#pragma unroll
+        for (int m = 0; m < CV; ++m) c[q * CV + m] = tv[m];
+      }
+    }
+    int pd[P];
+    {
+      const uint2 *pv = reinterpret_cast<const uint2 *>(pd_s + xb);
+#pragma unroll
+      for (int q = 0; q < P / 4; ++q) {
+        const uint2 t = pv[q];
+        pd[4 * q] = (int16_t)(t.x & 0xffffu);
+        pd[4 * q + 1] = (int16_t)(t.x >> 16);
+        pd[4 * q + 2] = (int16_t)(t.y & 0xffffu);
+        pd[4 * q + 3] = (int16_t)(t.y >> 16);
+      }
+    }
+    const int x = x0 + xb;
+    uint32_t o[P][DPL];
     if (x >= Dp - 1 && k.D == Dp) {
       // every d has x - d >= 0 and is a real disparity
-      uint32_t h[DPL];
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) o[i] = h[i] = (uint32_t)hamming<CT>(c, v[DPL - 1 - i]);
-      if (pd >= 0) {
-        // the far class for every cell, then the (at most three) cells with
-        // |d - prior| <= 1, in the one or two lanes that hold them
+      for (int u = 0; u < P; ++u) {
+        uint32_t h[DPL];
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) o[i] = tab_s[2 * 64 + h[i]];
-        if (pd + 1 >= d0 && pd - 1 < d0 + DPL) {
+        for (int i = 0; i < DPL; ++i) o[u][i] = h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
+        if (pd[u] >= 0) {
+          // the far class for every cell, then the (at most three) cells with
+          // |d - prior| <= 1, in the one or two lanes that hold them
 #pragma unroll
-          for (int i = 0; i < DPL; ++i) {
-            const int dd = d0 + i - pd;
-            if (dd >= -1 && dd <= 1) o[i] = tab_s[(dd != 0) * 64 + h[i]];
+          for (int i = 0; i < DPL; ++i) o[u][i] = tab_s[2 * 64 + h[i]];
+          if (pd[u] + 1 >= d0 && pd[u] - 1 < d0 + DPL) {
+#pragma unroll
+            for (int i = 0; i < DPL; ++i) {
+              const int dd = d0 + i - pd[u];
+              if (dd >= -1 && dd <= 1) o[u][i] = tab_s[(dd != 0) * 64 + h[i]];
+            }
           }
         }
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) {
-        const int d = d0 + i;
-        const int h = x >= d ? hamming<CT>(c, v[DPL - 1 - i]) : k.nbits;
-        const int cls = pd < 0 ? 3 : min(abs(d - pd), 2);
-        o[i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
-      }
+      for (int u = 0; u < P; ++u)
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+          const int d = d0 + i;
+          const int h = x + u >= d ? hamming<CT>(c[u], e[DPL - 1 + u - i]) : k.nbits;
+          const int cls = pd[u] < 0 ? 3 : min(abs(d - pd[u]), 2);
+          o[u][i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
+        }
     }
-    store_cost_bytes<DPL>(out + (size_t)px * Dp, o);
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+      if (xb + u < npx) store_cost_bytes<DPL>(out + (size_t)(xb + u) * Dp, o[u]);
   }
 }
 
@@ -569,11 +619,11 @@ static cudaError_t launch_cost_t(const KParams &k, const Buffers &b, int nf, con
   const int segmax = 8 * k.cost_px;
   const int nseg = (k.W + segmax - 1) / segmax, seg = (k.W + nseg - 1) / nseg;
   const int Dp = k.Dp;
-  const int VL = sizeof(CT) == 8 ? 2 : (k.DPL % 4 == 0 ? 4 : 2);
-  const int nwin = (seg + Dp + 3) / 4 * 4;                 // copy length, rows 16-byte aligned
-  const size_t smem = (size_t)VL * nwin * sizeof(CT) + (size_t)seg * sizeof(CT) + (size_t)seg * 4 + 256;
+  const int segr = (seg + kCostPix - 1) / kCostPix * kCostPix;
+  const int nwin = (segr + Dp + 3) / 4 * 4;                 // window entries, 16-byte multiple
+  const size_t smem = (size_t)nwin * sizeof(CT) + (size_t)segr * sizeof(CT) + (size_t)segr * 2;
   dim3 grid(nseg, k.H, nf);
-  // at most 2 x (1024 + 256) u64 entries + the segment's arrays: below the 48 KiB default
+  // at most (1024 + 256 + 4) + 1024 u64 entries + the priors: below the 48 KiB default
   if (smem > 48 * 1024) return cudaErrorInvalidConfiguration;
   auto launch = [&](auto kern) -> cudaError_t {
     kern<<<grid, 256, smem, s>>>(k, b, tab, seg, nwin);

@@ -55,8 +55,9 @@ struct Buffers {   // base pointers of frame 0
   int16_t *dbar, *dhat, *dstar, *dprime;
   int16_t *dsub;              // sub-pixel disparity (1/16 px)
   void *censL, *censR;        // u32 or u64 per pixel
-  uint32_t *boxS, *boxC;      // [MW][H][W] box-ORed presence masks, radii r_s and r_c
-  uint32_t *boxTmp;           // row-pass results of both radii: [2][F][MW][H][W]
+  uint32_t *boxS;             // [MW][H][W] box-ORed presence masks, radius r_s
+  uint32_t *boxC;             // [MW][H][W] their row ORs only (|x' - x| <= r_c), radius r_c
+  uint32_t *boxTmp;           // [F][MW][H][W] r_s row-pass results (scratch of the column pass)
   uint8_t *cost;              // [H][W][Dp]
   uint16_t *part[3];          // [H][W][Dp]
   void *spill;                // 4 regions (vertical, diag, anti-diag, rows) of H*W*Dp elements
@@ -260,6 +261,8 @@ cudaError_t launch_census(const KParams &k, const Buffers &b, int nf, int zoff, 
 // null; tmp holds nf * MW * H * W words per wanted radius
 cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t *tmp, uint32_t *boxS,
                          uint32_t *boxC, cudaStream_t s, const int *gate = nullptr);
+cudaError_t launch_boxor_cols(const KParams &k, int nf, const uint32_t *src, uint32_t *dst, int r, cudaStream_t s,
+                              const int *gate = nullptr);
 cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_cost(const KParams &k, const Buffers &b, int nf, cudaStream_t s);
 cudaError_t launch_agg_lines(const KParams &k, const Buffers &b, int nf, bool spill8, cudaStream_t s);

@@ -26,7 +26,8 @@
 namespace sgmf {
 
 // 8 Mi 32-bit words (32 MiB): three [MW][H][W] planes (d-bar in the first,
-// the row-pass results, the box-OR); with D <= 128 (MW <= 4) that holds
+// the second spare, the r_c row ORs of the presence masks in the third,
+// which the check kernel ORs over the window's rows); with D <= 128 (MW <= 4) that holds
 // frames of up to about 700 000 pixels.
 constexpr size_t kStaticScratchWords = size_t(8) << 20;
 static __device__ __align__(256) uint32_t g_check_scratch[kStaticScratchWords];
@@ -152,7 +153,7 @@ extern "C" sgmf_status sgmf_check_static(int width, int height, int max_disp, co
     return fail_static(SGMF_ERR_CUDA, std::string("sgmf_check_static: cudaGetSymbolAddress failed: ") +
                                           cudaGetErrorString(e));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  // d-bar (int16, the first half plane), the row-pass results, the box-OR
+  // d-bar (int16, the first half plane), a spare plane, the r_c row ORs
   int16_t *dbar = reinterpret_cast<int16_t *>(scratch);
   uint32_t *tmp = scratch + plane, *box = scratch + 2 * plane;
   dim3 grid((width + 31) / 32, (height + 7) / 8);
