@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <cstdint>
 
+#include "sgmf_cost.cuh"
 #include "sgmf_internal.cuh"
 
 namespace sgmf {
@@ -456,23 +457,10 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 // a pixel, a warp's stores one contiguous row of the cost volume.  (Eight
 // pixels a step, for fewer loop and load instructions, ran 14 % slower: the
 // registers they need halve the resident warps.)
-constexpr int kCostPix = 4;   // pixels a warp takes at a time
-
-template <typename CT, int DPL>
-struct CostWin {
-  static constexpr int P = kCostPix;
-  static constexpr int VL = sizeof(CT) == 8 ? 2 : (DPL % 4 == 0 ? 4 : 2);   // entries per vector load
-  using V = typename std::conditional<VL * sizeof(CT) == 16, uint4, uint2>::type;
-  static constexpr int NE = (P + DPL - 1 + VL - 1) / VL * VL;             // entries loaded (= P + DPL)
-  static_assert(P % 4 == 0 && DPL % 2 == 0, "aligned window, census and prior loads");
-};
-
 template <typename CT, int DPL, bool SEMI>
 __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const __grid_constant__ CostTable tab,
                                                   int seg, int nwin) {
-  using CW = CostWin<CT, DPL>;
-  constexpr int Dp = 32 * DPL, P = CW::P;
-  constexpr int VL = CW::VL, NE = CW::NE;
+  constexpr int Dp = 32 * DPL, P = kCostPix;
   __shared__ uint8_t tab_s[4 * 64];                           // fixed address: LDS [h + const]
   extern __shared__ __align__(16) uint8_t cs_smem[];
   const int segr = (seg + P - 1) / P * P;
@@ -535,78 +523,10 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
   __syncthreads();
   // (2) the cost bytes, four pixels per warp at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int d0 = DPL * lane;
-  uint8_t *out = b.cost + (rowp + x0) * Dp + d0;
+  uint8_t *out = b.cost + (rowp + x0) * Dp + DPL * lane;
   for (int xb = P * warp; xb < npx; xb += P * nwarp) {
-    // cR(x - d) for pixel xb + u and d = d0 + i is entry jlo + DPL - 1 + u - i
-    const int jlo = xb + DPL * (31 - lane);
-    CT e[NE];
-#pragma unroll
-    for (int q = 0; q < NE / VL; ++q) {
-      const typename CW::V t = reinterpret_cast<const typename CW::V *>(cr_s + jlo)[q];
-      const CT *tv = reinterpret_cast<const CT *>(&t);
-#pragma unroll
-      for (int m = 0; m < VL; ++m) e[q * VL + m] = tv[m];
-    }
-    CT c[P];
-    {
-      // 16-byte aligned: xb is a multiple of P
-      constexpr int CV = 16 / sizeof(CT);
-      const uint4 *cv = reinterpret_cast<const uint4 *>(cl_s + xb);
-#pragma unroll
-      for (int q = 0; q < P / CV; ++q) {
-        const uint4 t = cv[q];
-        const CT *tv = reinterpret_cast<const CT *>(&t);
-#pragma unroll
-        for (int m = 0; m < CV; ++m) c[q * CV + m] = tv[m];
-      }
-    }
-    int pd[P];
-    {
-      const uint2 *pv = reinterpret_cast<const uint2 *>(pd_s + xb);
-#pragma unroll
-      for (int q = 0; q < P / 4; ++q) {
-        const uint2 t = pv[q];
-        pd[4 * q] = (int16_t)(t.x & 0xffffu);
-        pd[4 * q + 1] = (int16_t)(t.x >> 16);
-        pd[4 * q + 2] = (int16_t)(t.y & 0xffffu);
-        pd[4 * q + 3] = (int16_t)(t.y >> 16);
-      }
-    }
-    const int x = x0 + xb;
     uint32_t o[P][DPL];
-    if (x >= Dp - 1 && k.D == Dp) {
-      // every d has x - d >= 0 and is a real disparity
-#pragma unroll
-      for (int u = 0; u < P; ++u) {
-        uint32_t h[DPL];
-#pragma unroll
-        for (int i = 0; i < DPL; ++i) o[u][i] = h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
-        if (pd[u] >= 0) {
-          // the far class for every cell, then the (at most three) cells with
-          // |d - prior| <= 1, in the one or two lanes that hold them
-#pragma unroll
-          for (int i = 0; i < DPL; ++i) o[u][i] = tab_s[2 * 64 + h[i]];
-          if (pd[u] + 1 >= d0 && pd[u] - 1 < d0 + DPL) {
-#pragma unroll
-            for (int i = 0; i < DPL; ++i) {
-              const int dd = d0 + i - pd[u];
-              if (dd >= -1 && dd <= 1) o[u][i] = tab_s[(dd != 0) * 64 + h[i]];
-            }
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int u = 0; u < P; ++u)
-#pragma unroll
-        for (int i = 0; i < DPL; ++i) {
-          const int d = d0 + i;
-          const int h = x + u >= d ? hamming<CT>(c[u], e[DPL - 1 + u - i]) : k.nbits;
-          const int cls = pd[u] < 0 ? 3 : min(abs(d - pd[u]), 2);
-          o[u][i] = d < k.D ? tab_s[cls * 64 + h] : 0u;
-        }
-    }
+    cost_quad<CT, DPL>(cr_s, cl_s, pd_s, xb, x0 + xb, lane, k.D, k.nbits, tab_s, o);
 #pragma unroll
     for (int u = 0; u < P; ++u)
       if (xb + u < npx) store_cost_bytes<DPL>(out + (size_t)(xb + u) * Dp, o[u]);
