@@ -673,7 +673,7 @@ struct RowGeom {
 
 // one chunk of lockstep steps [t_lo, t_hi); SECOND: the half where S is formed;
 // RESTART: the chunk holds the first step of a walk
-template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART, bool BANDED>
+template <int CPL, bool S8, int NP, bool FULLD, bool SECOND, bool RESTART, bool BANDED, bool FULL>
 __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, const uint8_t *stg, int xl, int t_lo,
                                           int t_hi, const uint32_t (&z)[CPL / 4], uint32_t (&kb)[CPL / 2],
                                           const StepConsts &sc, uint32_t edge_lo, uint32_t edge_hi, int grp, int lig,
@@ -688,9 +688,11 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
   // three directions each
   constexpr bool kPartBytes = S8 && NP != 2;   // byte vectors, else u16 sums
   const uint8_t *pst = stg + CF::kCost + CF::kSpill + lig * CPL * (kPartBytes ? 1 : 2);
-  for (int t = t_lo; t < t_hi; ++t) {
+  // one step at t; FULL: a chunk of K steps whose pixels are all in the
+  // image (both groups), unrolled
+  auto step_at = [&](const int t) {
     const int x = g.fwd ? t - g.delay : g.W - 1 - t;
-    const bool valid = x >= 0 && x < g.W;
+    const bool valid = FULL || (x >= 0 && x < g.W);
     const int r = valid ? x - xl : 0;
     uint32_t C[NW];
     unpack_u8<CPL>(cst + r * Dp, z, C);
@@ -721,7 +723,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
     w.mm = group_min<NW>(w.L, grp);
     if (!SECOND) {
       if (valid) spill_put<CPL, S8>(spill_lane + (size_t)x * Dp * SB, w.L);
-      continue;
+      return;
     }
     uint32_t Sm[NW];
     spill_get<CPL, S8>(sst + r * Dp * SB, Sm);
@@ -815,7 +817,7 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
           for (int j = 0; j < CPL; ++j) w.acc[j] = nacc[j];
         }
       }
-      continue;
+      return;
     }
     // right view: group 0 (x rising) moves keys up a slot per step, group 1
     // (x falling) down a slot; both fold in S(x, d)
@@ -854,6 +856,12 @@ __device__ __forceinline__ void row_chunk(RowWalk<CPL> &w, const RowGeom &g, con
           atomicMin(&merge[xr - g.mbase], v);
       }
     }
+  };
+  if constexpr (FULL) {
+#pragma unroll
+    for (int u = 0; u < CF::K; ++u) step_at(t_lo + u);
+  } else {
+    for (int t = t_lo; t < t_hi; ++t) step_at(t);
   }
 }
 
@@ -985,13 +993,27 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
     const uint8_t *stg = smem + (c % S) * CF::kStage + grp * CF::kGroup;
     // a walk starts at step delay (group 0) or 0 (group 1)
     const bool restart = t_lo <= g.delay && 0 < t_hi;
-#define ROW_CHUNK(SEC, RS)                                                                                   \
-  row_chunk<CPL, S8, NP, FULLD, SEC, RS, BANDED>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp,  \
-                                                 lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs, abuf)
+#define ROW_CHUNK(SEC, RS, FU)                                                                               \
+  row_chunk<CPL, S8, NP, FULLD, SEC, RS, BANDED, FU>(w, g, stg, xl, t_lo, t_hi, z, kb, sc, edge_lo, edge_hi, grp, \
+                                                     lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs, abuf)
+    // a full chunk: K steps, every pixel of both groups in the image
+    constexpr bool kFullChunks = true;
+    const bool full = kFullChunks && !BANDED && !restart && t_hi - t_lo == K && t_lo >= g.delay &&
+                      t_hi - 1 - g.delay < W && t_hi - 1 < W;
     if (c < c1) {
-      if (restart) ROW_CHUNK(false, true); else ROW_CHUNK(false, false);
+      if (restart)
+        ROW_CHUNK(false, true, false);
+      else if (full)
+        ROW_CHUNK(false, false, true);
+      else
+        ROW_CHUNK(false, false, false);
     } else {
-      if (restart) ROW_CHUNK(true, true); else ROW_CHUNK(true, false);
+      if (restart)
+        ROW_CHUNK(true, true, false);
+      else if (full)
+        ROW_CHUNK(true, false, true);
+      else
+        ROW_CHUNK(true, false, false);
     }
 #undef ROW_CHUNK
     __syncwarp();

@@ -507,7 +507,9 @@ static sgmf_status front_stages(sgmf_ctx *c, int f0, int nf, const uint8_t *left
   if (k.semidense || need_boxc(k)) {
     // both windows' row pass at once; the column pass for r_s (Eq. 5) into
     // boxS, from the row results of frames [f0, f0 + nf) in their own part
-    // of boxTmp; the r_c row ORs (Eq. 6) stay in boxC for the check
+    // of boxTmp; the r_c row ORs (Eq. 6) stay in boxC for the check.  (On
+    // the side stream beside the census it saved 0.01 ms of 8.18 for 32
+    // KITTI frames: the two run one after the other all the same.)
     TIMED(c, "boxor", s, launch_boxor(k, nf, bp.dbar, c->b.boxTmp + (size_t)f0 * k.MW * px,
                                       k.semidense ? bp.boxS : nullptr, need_boxc(k) ? bp.boxC : nullptr, s,
                                       bp.gate));
