@@ -998,7 +998,7 @@ __global__ void __launch_bounds__(32) k_agg_rows(const __grid_constant__ RowArgs
                                                      lig, spill_lane, dstar, dprime, dsub, dbg_lane, merge, bs, abuf)
     // a full chunk: K steps, every pixel of both groups in the image
     constexpr bool kFullChunks = true;
-    const bool full = kFullChunks && !BANDED && !restart && t_hi - t_lo == K && t_lo >= g.delay &&
+    const bool full = kFullChunks && !restart && t_hi - t_lo == K && t_lo >= g.delay &&
                       t_hi - 1 - g.delay < W && t_hi - 1 < W;
     if (c < c1) {
       if (restart)

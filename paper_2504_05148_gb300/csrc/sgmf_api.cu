@@ -235,6 +235,18 @@ extern "C" sgmf_status sgmf_create(int width, int height, int max_disp, sgmf_ctx
   return sgmf_create_batched(width, height, max_disp, 1, out);
 }
 
+// the side stream of the row kernels and checks of a batch in parts, at the
+// priority of a default stream (kSidePriority = 1, above it, was measured:
+// 8.14-8.21 against 8.12 ms for 32 KITTI frames -- the row kernels got ahead,
+// the sweep fell behind by as much)
+static cudaError_t side_stream(cudaStream_t *s) {
+  constexpr int kSidePriority = 0;
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, kSidePriority ? greatest : least);
+}
+
 static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch, int band, sgmf_ctx **out) {
   if (!out) return fail(nullptr, SGMF_ERR_ARG, "sgmf_create: out is NULL");
   *out = nullptr;
@@ -321,7 +333,7 @@ static sgmf_status create_ctx(int width, int height, int max_disp, int max_batch
     c->k.sweep_cs = agg_sweep_plan(kk, c->nb, &c->sweep_slots);
     c->sweep_ok = c->k.sweep_cs > 0;
     bool ok = !(c->sweep_ok && c->nb >= 2) ||
-              (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+              (side_stream(&c->side) == cudaSuccess &&
                cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess);
     for (int i = 0; ok && c->side && i < sgmf_ctx::kMaxParts; ++i)
