@@ -76,13 +76,19 @@ __device__ __forceinline__ void cost_quad(const CT *cr, const CT *cl, const int1
       pd[4 * q + 3] = (int16_t)(t.y >> 16);
     }
   }
-  if (x >= Dp - 1 && D == Dp) {
-    // every d has x - d >= 0 and is a real disparity
+  if (D == Dp) {
+    // every d is a real disparity; near the left border the cells with
+    // x - d < 0 take the full census length
+    const bool edge = x < Dp - 1;
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       uint32_t h[DPL];
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) o[u][i] = h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
+      for (int i = 0; i < DPL; ++i) {
+        h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
+        if (edge && x + u < d0 + i) h[i] = (uint32_t)nbits;
+        o[u][i] = h[i];
+      }
       if (pd[u] >= 0) {
         // the far class for every cell, then the (at most three) cells with
         // |d - prior| <= 1, in the one or two lanes that hold them

@@ -476,6 +476,20 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
   const CT *cl = static_cast<const CT *>(b.censL) + rowp;
   const CT *cr = static_cast<const CT *>(b.censR) + rowp;
   const int base = x0 - (Dp - 1);
+  // the d-bar and r_s mask words (MW = DPL) of the thread's pixels
+  // tid + 256 j, loaded first so that their latency overlaps the staging
+  constexpr int PPT = 4;   // pixels a thread takes at most (segments of <= 1024 pixels)
+  const size_t plane = (size_t)W * k.H;
+  int16_t db_r[PPT];
+  uint32_t mw_r[PPT][DPL];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int i = threadIdx.x + 256 * j;
+    const size_t p = rowp + x0 + i;
+    db_r[j] = i < npx ? b.dbar[p] : (int16_t)-1;
+#pragma unroll
+    for (int w = 0; w < DPL; ++w) mw_r[j][w] = (SEMI && i < npx) ? b.boxS[w * plane + p] : 0u;
+  }
   for (int j = threadIdx.x; j < nwin; j += blockDim.x) {
     const int xx = base + j;
     cr_s[j] = (xx >= 0 && xx < W) ? cr[xx] : (CT)0;
@@ -484,26 +498,25 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
   for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) tab_s[i] = (&tab.v[0][0])[i];
   __syncthreads();
   // (1) the prior of every pixel of the segment
-  const size_t plane = (size_t)W * k.H;
-  for (int i = threadIdx.x; i < npr; i += blockDim.x) {
+#pragma unroll
+  for (int jj = 0; jj < PPT; ++jj) {
+    const int i = threadIdx.x + 256 * jj;
+    if (i >= npr) break;
     if (i >= npx) {
       pd_s[i] = -1;
       continue;
     }
     const size_t p = rowp + x0 + i;
-    const int db = b.dbar[p];
+    const int db = db_r[jj];
     int pd = db;
     if (SEMI) {
       const int x = x0 + i;
       const CT c = cl_s[i];
-      uint32_t mw[8];
-#pragma unroll
-      for (int w = 0; w < 8; ++w) mw[w] = w < k.MW ? b.boxS[w * plane + p] : 0u;
       int best_h = 0x7fffffff, best_d = -1;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        if (w >= k.MW || best_h == 0) break;
-        uint32_t m = mw[w];
+      for (int w = 0; w < DPL; ++w) {
+        if (best_h == 0) break;
+        uint32_t m = mw_r[jj][w];
         while (m != 0u) {
           const int d = w * 32 + __ffs(m) - 1;
           m &= m - 1u;
@@ -535,8 +548,8 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
 
 template <typename CT, bool SEMI>
 static cudaError_t launch_cost_t(const KParams &k, const Buffers &b, int nf, const CostTable &tab, cudaStream_t s) {
-  // segments of at most 8 x cost_px pixels, equal lengths
-  const int segmax = 8 * k.cost_px;
+  // segments of at most 8 x cost_px pixels (at most 1024: four a thread in the Eq. 5 step), equal lengths
+  const int segmax = min(8 * k.cost_px, 1024);
   const int nseg = (k.W + segmax - 1) / segmax, seg = (k.W + nseg - 1) / nseg;
   const int Dp = k.Dp;
   const int segr = (seg + kCostPix - 1) / kCostPix * kCostPix;
