@@ -68,9 +68,15 @@ struct SweepCfg {
   static constexpr int kExclusive = 120 * 1024;
   // ring, barriers, exchange slots, one band-shift buffer (Dp u16) and the
   // edge words of its 3P + 2 vectors (two words each) per group
+  // the plain sweep's sums leave by bulk copies (Dp <= 128: the buffers fit
+  // beside the ring): per warp two staging buffers (by row parity) of its
+  // 2 P pixels' u16 sums
+  static constexpr bool kBulkSums = !BANDED && CPL <= 8;
+  static constexpr int kSumBuf = 2 * P * Dp;   // u16 elements of one buffer
   static constexpr int smem_bytes(int warps) {
     return max(kExclusive, R * (2 * warps * P) * Dp + (R + 5) * 8 + 2 * 2 * (2 * warps) * kSlot * 4 +
-                               (2 * warps) * Dp * 2 + (2 * warps) * (3 * P + 2) * 2 * 4);
+                               (2 * warps) * Dp * 2 + (2 * warps) * (3 * P + 2) * 2 * 4 +
+                               (kBulkSums ? warps * 2 * kSumBuf * 2 + 128 : 0));
   }
 };
 
@@ -253,8 +259,15 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
   // them (sgm_step_e), [vector][lane 0 / lane 15]: V[i] = i, DL[i] = P + i,
   // DR[i] = 2P + i, the vector entering from the left 3P, from the right 3P + 1
   constexpr int NE = 3 * P + 2;
-  uint32_t *esm = reinterpret_cast<uint32_t *>(reinterpret_cast<uint16_t *>(slots + 2 * 2 * ng * SL) + ng * Dp) +
-                  gi * NE * 2 + (lig == 15 ? 1 : 0);
+  uint32_t *esm0 = reinterpret_cast<uint32_t *>(reinterpret_cast<uint16_t *>(slots + 2 * 2 * ng * SL) + ng * Dp);
+  uint32_t *esm = esm0 + gi * NE * 2 + (lig == 15 ? 1 : 0);
+  // the warp's sum staging buffers (kBulkSums), after the edge words, 128-byte aligned
+  uint16_t *wsum = reinterpret_cast<uint16_t *>((reinterpret_cast<uintptr_t>(esm0 + ng * NE * 2) + 127) &
+                                                ~uintptr_t(127)) +
+                   (size_t)warp * 2 * CF::kSumBuf;
+  uint16_t *sum_base = a.sum[up ? 1 : 0] + f * fcells;   // the launch frame's sums
+  const int xw = x_cta + warp * 2 * P;                   // the warp's first pixel
+  const int nvw = max(0, min(2 * P, W - xw));            // its pixels inside the image
   // re-index a vector to this row's band and record its edge word (lanes 0 and 15)
   auto shift_rec = [&](uint32_t(&v)[NW], int delta, int k) {
     uint32_t e = 0xffffffffu;
@@ -435,7 +448,13 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
           step(DR[P - 1], mR[P - 1], inR, minR, C, edge(3 * P + 1));
         }
         const int x = xg + i;
-        if (ok && x < W) {
+        if constexpr (CF::kBulkSums) {
+          // into the row's staging buffer (pixels outside the image are not copied out)
+          uint32_t sum[NW];
+#pragma unroll
+          for (int w = 0; w < NW; ++w) sum[w] = V[i][w] + DL[i][w] + DR[i][w];
+          store_u16<CPL>(wsum + (t & 1) * CF::kSumBuf + (grp * P + i) * Dp + lig * CPL, sum);
+        } else if (ok && x < W) {
           uint32_t sum[NW];
 #pragma unroll
           for (int w = 0; w < NW; ++w) sum[w] = V[i][w] + DL[i][w] + DR[i][w];
@@ -447,6 +466,22 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
       row(std::true_type{});
     else
       row(std::false_type{});
+    if constexpr (CF::kBulkSums) {
+      // the row's sums of the warp's pixels: one bulk copy from the staging
+      // buffer; the buffer of row t - 1 has been read before row t + 1 reuses it
+      fence_proxy_async_shared();
+      __syncwarp();
+      if (lane == 0) {
+        if (ok && nvw > 0)
+          bulk_s2g(sum_base + ((size_t)y * W + xw) * Dp, wsum + (t & 1) * CF::kSumBuf, (uint32_t)(nvw * Dp * 2));
+        bulk_commit();
+        bulk_wait_read_all_but_one();
+      }
+      __syncwarp();
+    }
+  }
+  if constexpr (CF::kBulkSums) {
+    if (lane == 0) bulk_wait_all();
   }
   // every message was waited for by its receiver; the cluster barrier keeps
   // every CTA (and its shared memory) alive until all are done
