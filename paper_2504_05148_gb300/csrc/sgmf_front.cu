@@ -101,6 +101,53 @@ __device__ __forceinline__ uint64_t census_bits(const uint8_t (*T)[kCenBoxW], in
   return c;
 }
 
+// The centre-symmetric census of four horizontally adjacent pixels of an
+// interior tile at once, four byte lanes per 32-bit word.  For each offset
+// the four pixels' samples I(p+o) and I(p-o) are four consecutive bytes of a
+// staged row (byte permutes of three aligned words per row); the per-byte
+// unsigned comparison is made with ordinary integer operations: with H the
+// bytes' high bits, (b | H) - (a & ~H) borrows across no byte and its high
+// bit says low(b) >= low(a), so b >= a is (b & ~a) | (~(a ^ b) & that) on the
+// high bits, and a > b its complement.  The offsets' bits are shifted into
+// four accumulators of eight offsets each (one bit per byte lane per
+// offset), which a byte transpose turns into the four descriptors.
+__device__ __forceinline__ uint32_t bytes_gt(uint32_t a, uint32_t b) {
+  constexpr uint32_t H = 0x80808080u;
+  const uint32_t d = (b | H) - (a & ~H);
+  const uint32_t ge = (b & ~a) | (~(a ^ b) & d);
+  return ~ge & H;   // high bit of byte j: a_j > b_j
+}
+
+// bytes off .. off + 3 of the 12 bytes w[0..2] (off in 0..8, a constant)
+__device__ __forceinline__ uint32_t bytes_at(const uint32_t (&w)[3], int off) {
+  const int i = off >> 2, sh = off & 3;
+  return sh == 0 ? w[i] : __byte_perm(w[i], w[i + 1], 0x3210u + 0x1111u * (uint32_t)sh);
+}
+
+// descriptors of the tile pixels (sx .. sx + 3, sy) of one staged box
+__device__ __forceinline__ void census_cs4(const uint8_t *box, int sx, int sy, uint32_t (&desc)[4]) {
+  uint32_t acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int dy = 0; dy >= -3; --dy) {
+    const uint32_t *ra = reinterpret_cast<const uint32_t *>(box + (sy + dy) * kCenBoxW + sx - 4);
+    const uint32_t *rb = reinterpret_cast<const uint32_t *>(box + (sy - dy) * kCenBoxW + sx - 4);
+    const uint32_t A[3] = {ra[0], ra[1], ra[2]}, B[3] = {rb[0], rb[1], rb[2]};
+#pragma unroll
+    for (int dx = 4; dx >= -4; --dx) {
+      if (dy == 0 && dx >= 0) continue;   // the half before the centre
+      const int kbit = (dy + 3) * 9 + (dx + 4);   // offsets visited in decreasing k
+      const uint32_t gt = bytes_gt(bytes_at(A, dx + 4), bytes_at(B, 4 - dx));
+      acc[kbit >> 3] = acc[kbit >> 3] * 2u + (gt >> 7);
+    }
+  }
+  const uint32_t lo = __byte_perm(acc[0], acc[1], 0x5140), hi = __byte_perm(acc[2], acc[3], 0x5140);
+  const uint32_t lo2 = __byte_perm(acc[0], acc[1], 0x7362), hi2 = __byte_perm(acc[2], acc[3], 0x7362);
+  desc[0] = __byte_perm(lo, hi, 0x5410);
+  desc[1] = __byte_perm(lo, hi, 0x7632);
+  desc[2] = __byte_perm(lo2, hi2, 0x5410);
+  desc[3] = __byte_perm(lo2, hi2, 0x7632);
+}
+
 // b0 holds the buffers of the launch's first frame, which is frame zoff of
 // the tensor maps (their third coordinate)
 template <bool FULL>
@@ -131,6 +178,22 @@ __global__ void __launch_bounds__(256) k_census(KParams k, Buffers b0, int zoff,
     return;
   }
   const bool interior = x0 >= 4 && x0 + kCenTileW + 4 <= k.W && y0 >= 3 && y0 + kCenTileH + 3 <= k.H;
+  if (!FULL && interior) {
+    // four pixels a thread: 16 threads a tile row, 16 rows
+    static_assert(kCenTileW == 64 && kCenTileH == 16, "census_cs4 covers the tile with 256 threads");
+    const int g = threadIdx.x & 15, r = threadIdx.x >> 4;
+    const int x = x0 + 4 * g, y = y0 + r;
+    const size_t p = (size_t)y * k.W + x;
+#pragma unroll
+    for (int img = 0; img < 2; ++img) {
+      uint32_t d[4];
+      census_cs4(tiles + img * kBoxBytes, 4 * g + 16, r + 3, d);
+      uint32_t *o = static_cast<uint32_t *>(img ? b.censR : b.censL) + p;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u] = d[u];
+    }
+    return;
+  }
   const int tx = threadIdx.x & 63;
   const int x = x0 + tx;
   for (int r = threadIdx.x >> 6; r < kCenTileH; r += 4) {
