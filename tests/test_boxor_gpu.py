@@ -44,6 +44,9 @@ def _masks(scene, params):
     (97, 130, 256, 3, 40, 0.3),        # 8 word planes, windows taller than a column tile
     (33, 17, 64, 0, 1, 1.0),           # a LiDAR value at every pixel
     (300, 200, 192, 255, 100, 0.02),   # the largest radius
+    (200, 90, 128, 16, 16, 0.1),       # equal radii
+    (130, 70, 256, 16, 3, 0.2),        # r_s above r_c, 8 word planes
+    (150, 33, 128, 17, 4, 0.1),        # column segments of 32 rows and a ragged last one
     (1, 70, 16, 2, 5, 0.5),            # one column
     (70, 1, 100, 5, 7, 0.5),           # one row
 ])
