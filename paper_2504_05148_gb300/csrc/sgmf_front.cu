@@ -45,10 +45,66 @@ __global__ void __launch_bounds__(256) k_ingest(KParams k, Buffers b0, const uin
   b.imgR[(size_t)y * k.pitch + x] = right[p];
 }
 
+// d-bar of one LiDAR sample (0 = no return, non-finite or beyond D-1: -1)
+__device__ __forceinline__ int lidar_dbar(float f, int D) {
+  if (isfinite(f) && f > 0.0f) {
+    const float r = rintf(f);
+    if (r <= (float)(D - 1)) return (int)r;
+  }
+  return -1;
+}
+
+// The same for even W, four pixels a thread: with y W even, the LiDAR row
+// is read as 8-byte pairs, the image rows as 2-byte pairs, d-bar written as
+// 4-byte pairs and the pitched rows as 4-byte words (pitch % 16 == 0).
+__global__ void __launch_bounds__(256) k_ingest4(KParams k, Buffers b0, const uint8_t *__restrict__ left,
+                                                 const uint8_t *__restrict__ right, const float *__restrict__ lidar) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x = blockIdx.x * 128 + 4 * lane, y = blockIdx.y * 8 + warp;
+  if (x >= k.W || y >= k.H) return;
+  const int f = blockIdx.z;
+  const Buffers b = frame_view(k, b0, f);
+  if (gated_off(b.gate, k.gate_run)) return;
+  const size_t fo = (size_t)f * frame_px(k), p = (size_t)y * k.W + x;
+  left += fo;
+  right += fo;
+  if (lidar != nullptr) lidar += fo;
+  if (x + 3 < k.W) {
+    int v[4] = {-1, -1, -1, -1};
+    if (lidar != nullptr) {
+      const float2 l0 = *reinterpret_cast<const float2 *>(lidar + p);
+      const float2 l1 = *reinterpret_cast<const float2 *>(lidar + p + 2);
+      v[0] = lidar_dbar(l0.x, k.D), v[1] = lidar_dbar(l0.y, k.D);
+      v[2] = lidar_dbar(l1.x, k.D), v[3] = lidar_dbar(l1.y, k.D);
+    }
+    uint32_t *db = reinterpret_cast<uint32_t *>(b.dbar + p);
+    db[0] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+    db[1] = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+    const uint16_t *l2 = reinterpret_cast<const uint16_t *>(left + p);
+    const uint16_t *r2 = reinterpret_cast<const uint16_t *>(right + p);
+    *reinterpret_cast<uint32_t *>(b.imgL + (size_t)y * k.pitch + x) = (uint32_t)l2[0] | ((uint32_t)l2[1] << 16);
+    *reinterpret_cast<uint32_t *>(b.imgR + (size_t)y * k.pitch + x) = (uint32_t)r2[0] | ((uint32_t)r2[1] << 16);
+  } else {
+    for (int u = 0; x + u < k.W; ++u) {
+      b.dbar[p + u] = (int16_t)(lidar != nullptr ? lidar_dbar(lidar[p + u], k.D) : -1);
+      b.imgL[(size_t)y * k.pitch + x + u] = left[p + u];
+      b.imgR[(size_t)y * k.pitch + x + u] = right[p + u];
+    }
+  }
+}
+
 cudaError_t launch_ingest(const KParams &k, const Buffers &b, int nf, const uint8_t *left, const uint8_t *right,
                           const float *lidar, cudaStream_t s) {
-  dim3 grid((k.W + 31) / 32, (k.H + 7) / 8, nf);
-  k_ingest<<<grid, 256, 0, s>>>(k, b, left, right, lidar);
+  // the four-pixel form needs even rows and 8-byte aligned inputs
+  const bool four = k.W % 2 == 0 && reinterpret_cast<uintptr_t>(left) % 2 == 0 &&
+                    reinterpret_cast<uintptr_t>(right) % 2 == 0 && reinterpret_cast<uintptr_t>(lidar) % 8 == 0;
+  if (four) {
+    dim3 grid((k.W + 127) / 128, (k.H + 7) / 8, nf);
+    k_ingest4<<<grid, 256, 0, s>>>(k, b, left, right, lidar);
+  } else {
+    dim3 grid((k.W + 31) / 32, (k.H + 7) / 8, nf);
+    k_ingest<<<grid, 256, 0, s>>>(k, b, left, right, lidar);
+  }
   return cudaGetLastError();
 }
 
