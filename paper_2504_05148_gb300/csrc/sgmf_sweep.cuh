@@ -447,14 +447,14 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
           mL[P - 1] = meL;
           step(DR[P - 1], mR[P - 1], inR, minR, C, edge(3 * P + 1));
         }
+        const int x = xg + i;
         if constexpr (CF::kBulkSums) {
           // into the row's staging buffer (pixels outside the image are not copied out)
           uint32_t sum[NW];
 #pragma unroll
           for (int w = 0; w < NW; ++w) sum[w] = V[i][w] + DL[i][w] + DR[i][w];
           store_u16<CPL>(wsum + (t & 1) * CF::kSumBuf + (grp * P + i) * Dp + lig * CPL, sum);
-        } else if (ok && xg + i < W) {
-          const int x = xg + i;
+        } else if (ok && x < W) {
           uint32_t sum[NW];
 #pragma unroll
           for (int w = 0; w < NW; ++w) sum[w] = V[i][w] + DL[i][w] + DR[i][w];
