@@ -27,7 +27,7 @@
 // cluster scope inside the row loop.
 //
 // Cost rows arrive by bulk copies (one per row and CTA: the strip's pixels
-// are contiguous) into a ring of R stages, four rows ahead.  Every mbarrier
+// are contiguous) into a ring of R stages, two rows ahead.  Every mbarrier
 // wait is bounded (the error word records a timeout); the two cluster
 // barriers, at the start and the end, are executed by every thread.
 #pragma once
@@ -61,7 +61,7 @@ struct SweepCfg {
   static constexpr int P = CPL <= 8 && !BANDED ? 8 : 4;
   static constexpr int kMaxWarps = CPL <= 8 ? (BANDED ? 20 : 8) : 10;
   static constexpr int kMaxCluster = 16;         // CTAs per cluster (above 8: non-portable)
-  static constexpr int R = 6;                    // ring stages (rows)
+  static constexpr int R = 4;                    // ring stages (rows)
   static constexpr int kSlot = (NW + 1) * 16;    // words of one exchanged vector: NW words + m, per lane
   // at least kExclusive bytes: one CTA per SM, so that the clusters the
   // device holds at once are the SMs the sweep occupies
@@ -196,8 +196,6 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
   if (threadIdx.x == 0) {
     issue(0);
     if (H > 1) issue(1);
-    if (H > 2) issue(2);
-    if (H > 3) issue(3);
   }
   // every CTA of the cluster runs, its barriers initialised, before the first remote store
   cluster_arrive();
@@ -364,7 +362,7 @@ __global__ void __launch_bounds__(32 * SweepCfg<CPL, BANDED>::kMaxWarps, 1)
         }
       }
       // the ring stage of row t - 2 is free: every warp finished that row before its row t - 1 arrival
-      if (threadIdx.x == 0 && issued < H && issued <= t + 4) issue(issued);
+      if (threadIdx.x == 0 && issued < H && issued <= t + 2) issue(issued);
       if (t + 1 < H) {
         // row t's outgoing vectors (the last row's have no reader)
         const int par = t & 1;
