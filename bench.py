@@ -111,7 +111,7 @@ KERNEL_SOURCES = {
     "agg_sweep": ("sgmf_sweep", "sgmf_aggregate", "sgmf_agg_cpl"),
     "agg_rows_wta": ("sgmf_aggregate", "sgmf_agg_cpl"),
     "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor": ("sgmf_front",),
-    "semidense": ("sgmf_front",), "cost": ("sgmf_front",),
+    "semidense": ("sgmf_front",), "cost": ("sgmf_front", "sgmf_cost"),
     "consistency": ("sgmf_check",),
 }
 
