@@ -104,14 +104,16 @@ def pipeline_roofline(rates: dict, sm_mhz: float, hbm_gbs: float, V: int, N: int
                     "sgmf_measure_rates on this GPU, x SMs x the sampled SM clock; frac = ideal / step time"}
 
 
-# csrc files whose contents decide each timed kernel's code and launch shape
-# (the shared header and the API file that sizes the buffers go with every one)
+# csrc files whose contents decide each timed kernel's code and launch shape:
+# the files that define and launch it and every header they include (the
+# shared header and the API file that sizes the buffers go with every one)
 KERNEL_SOURCES = {
-    "agg_lines": ("sgmf_aggregate", "sgmf_agg_cpl"),
+    "agg_lines": ("sgmf_sweep", "sgmf_aggregate", "sgmf_agg_cpl"),
     "agg_sweep": ("sgmf_sweep", "sgmf_aggregate", "sgmf_agg_cpl"),
-    "agg_rows_wta": ("sgmf_aggregate", "sgmf_agg_cpl"),
-    "ingest": ("sgmf_front",), "census": ("sgmf_front",), "boxor": ("sgmf_front",),
-    "semidense": ("sgmf_front",), "cost": ("sgmf_front", "sgmf_cost"),
+    "agg_rows_wta": ("sgmf_sweep", "sgmf_aggregate", "sgmf_agg_cpl"),
+    "ingest": ("sgmf_front", "sgmf_cost"), "census": ("sgmf_front", "sgmf_cost"),
+    "boxor": ("sgmf_front", "sgmf_cost"), "semidense": ("sgmf_front", "sgmf_cost"),
+    "cost": ("sgmf_front", "sgmf_cost"),
     "consistency": ("sgmf_check",),
 }
 
