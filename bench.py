@@ -732,6 +732,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-contexts", type=int, default=2, help="contexts taking the end-to-end steps in turn")
     ap.add_argument("--workload", default="kitti", choices=["kitti", "mixed", "serve", "learned"])
     ap.add_argument("--eval-frames", type=int, default=8)
     ap.add_argument("--learned-batch", type=int, default=1)
@@ -861,34 +862,37 @@ def main():
     value = frames_total * W * H * D / (total_ms * 1e-3)
 
     # end to end through the public host-buffer entry points (pinned host memory):
-    # two contexts on two streams take alternate steps, so one step's copies
-    # overlap the other's kernels; every step copies its 16 pairs in and its
-    # 16 outputs back
+    # --e2e-contexts contexts on as many streams take steps in turn, so one
+    # step's copies overlap another's kernels; every step copies its B pairs in
+    # and its B outputs back
     e2e = None
     latency = None
     if not args.no_e2e:
         hl = torch.from_numpy(np.stack([f.left for f in frames])).pin_memory().numpy()
         hr = torch.from_numpy(np.stack([f.right for f in frames])).pin_memory().numpy()
         hli = torch.from_numpy(np.stack([f.lidar for f in frames])).pin_memory().numpy()
-        ho = [torch.empty((B, H, W), dtype=torch.int16).pin_memory().numpy() for _ in range(2)]
+        nc = max(1, args.e2e_contexts)
+        ho = [torch.empty((B, H, W), dtype=torch.int16).pin_memory().numpy() for _ in range(nc)]
         ctx.set_profiling(False)
-        stream2 = torch.cuda.Stream(device=dev)
-        ctx2 = sgmf.Context(W, H, D, stream=stream2, max_batch=B)
-        if tuning is not None:
-            sgmf.sgmf_set_tuning(ctx2.handle, *tuning)
-        ctxs = [ctx, ctx2]
+        extra = []
+        for _ in range(nc - 1):
+            c = sgmf.Context(W, H, D, stream=torch.cuda.Stream(device=dev), max_batch=B)
+            if tuning is not None:
+                sgmf.sgmf_set_tuning(c.handle, *tuning)
+            extra.append(c)
+        ctxs = [ctx] + extra
 
         def e2e_steps(k):
             for i in range(k):
-                c = ctxs[i % 2]
-                if i >= 2:
+                c = ctxs[i % nc]
+                if i >= nc:
                     c.sync()
                 sgmf.sgmf_compute_host_batch_async(c.handle, B, hl.ctypes.data, hr.ctypes.data, hli.ctypes.data,
-                                                   ho[i % 2].ctypes.data)
+                                                   ho[i % nc].ctypes.data)
             for c in ctxs:
                 c.sync()
 
-        e2e_steps(max(args.warmup, 2))
+        e2e_steps(max(args.warmup, nc))
         if pg:
             import torch.distributed as dist
             dist.barrier()
@@ -907,13 +911,14 @@ def main():
         dt, dt_sync = float(te[0].item()), float(te[1].item())
         e2e = {"value": frames_total * W * H * D / dt, "unit": UNIT,
                "h2d_bytes_per_step": B * (W * H * 2 + W * H * 4), "d2h_bytes_per_step": B * W * H * 2,
-               "frames_per_s": frames_total / dt, "api": "sgmf_compute_host_batch_async, 2 contexts",
+               "frames_per_s": frames_total / dt, "api": f"sgmf_compute_host_batch_async, {nc} contexts",
                "sync_api_frames_per_s": frames_total / dt_sync}
         # the host results must equal the device results
         for o in ho:
             if not np.array_equal(o, dout.cpu().numpy()):
                 raise RuntimeError("host entry point result differs from the device result")
-        ctx2.close()
+        for c in extra:
+            c.close()
         # single-frame latency: one pair per call, device-timed and host to host
         c1 = sgmf.Context(W, H, D, stream=stream, max_batch=1)
         if not args.no_tune:
