@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "sgmf_internal.cuh"
 
@@ -77,32 +78,40 @@ __device__ __forceinline__ void cost_quad(const CT *cr, const CT *cl, const int1
     }
   }
   if (D == Dp) {
-    // every d is a real disparity; near the left border the cells with
-    // x - d < 0 take the full census length
-    const bool edge = x < Dp - 1;
+    // every d is a real disparity; near the left border (x < Dp - 1, the
+    // first pixels of a row only) the cells with x - d < 0 take the full
+    // census length: a separate copy of the step, so that the others carry no
+    // per-cell select
+    auto quad = [&](auto border) {
+      constexpr bool EDGE = decltype(border)::value;
 #pragma unroll
-    for (int u = 0; u < P; ++u) {
-      uint32_t h[DPL];
+      for (int u = 0; u < P; ++u) {
+        uint32_t h[DPL];
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) {
-        h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
-        if (edge && x + u < d0 + i) h[i] = (uint32_t)nbits;
-        o[u][i] = h[i];
-      }
-      if (pd[u] >= 0) {
-        // the far class for every cell, then the (at most three) cells with
-        // |d - prior| <= 1, in the one or two lanes that hold them
+        for (int i = 0; i < DPL; ++i) {
+          h[i] = (uint32_t)hamming<CT>(c[u], e[DPL - 1 + u - i]);
+          if (EDGE && x + u < d0 + i) h[i] = (uint32_t)nbits;
+          o[u][i] = h[i];
+        }
+        if (pd[u] >= 0) {
+          // the far class for every cell, then the (at most three) cells with
+          // |d - prior| <= 1, in the one or two lanes that hold them
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) o[u][i] = tab[2 * 64 + h[i]];
-        if (pd[u] + 1 >= d0 && pd[u] - 1 < d0 + DPL) {
+          for (int i = 0; i < DPL; ++i) o[u][i] = tab[2 * 64 + h[i]];
+          if (pd[u] + 1 >= d0 && pd[u] - 1 < d0 + DPL) {
 #pragma unroll
-          for (int i = 0; i < DPL; ++i) {
-            const int dd = d0 + i - pd[u];
-            if (dd >= -1 && dd <= 1) o[u][i] = tab[(dd != 0) * 64 + h[i]];
+            for (int i = 0; i < DPL; ++i) {
+              const int dd = d0 + i - pd[u];
+              if (dd >= -1 && dd <= 1) o[u][i] = tab[(dd != 0) * 64 + h[i]];
+            }
           }
         }
       }
-    }
+    };
+    if (x < Dp - 1)
+      quad(std::true_type{});
+    else
+      quad(std::false_type{});
   } else {
 #pragma unroll
     for (int u = 0; u < P; ++u)
