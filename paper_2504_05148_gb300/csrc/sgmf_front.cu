@@ -504,9 +504,9 @@ cudaError_t launch_boxor(const KParams &k, int nf, const int16_t *disp, uint32_t
 // --------------------------------------------------------------------------
 // Semidensification, Eq. 5 (Sec. IV-B).  The candidates of pixel p are the
 // distinct valid d-bar_q, q in the (2rs+1)^2 window: exactly the set bits of
-// the box-ORed presence mask.  Visiting them in increasing d and keeping the
-// first strict minimum of H(p, d) gives the smallest H with ties to the
-// smaller disparity.  d-hat = that d if min H < ts, else d-bar_p.
+// the box-ORed presence mask.  The smallest key H(p, d) << 9 | d over them is
+// the smallest H with ties to the smaller disparity.  d-hat = that d if
+// min H < ts, else d-bar_p.
 template <typename CT>
 __global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b0) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -523,23 +523,19 @@ __global__ void __launch_bounds__(256) k_semidense(KParams k, Buffers b0) {
   uint32_t mw[8];
 #pragma unroll
   for (int w = 0; w < 8; ++w) mw[w] = w < k.MW ? b.boxS[w * plane + p] : 0u;
-  int best_h = 0x7fffffff, best_d = -1;
+  uint32_t best = 0xffffffffu;
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    if (w >= k.MW || best_h == 0) break;
+    if (w >= k.MW || best < 512u) break;   // H = 0 found: no later candidate wins
     uint32_t m = mw[w];
     while (m != 0u) {
       const int d = w * 32 + __ffs(m) - 1;
       m &= m - 1u;
-      const int h = (x >= d) ? __popcll((uint64_t)(c ^ cr[p - d])) : k.nbits;
-      if (h < best_h) {
-        best_h = h;
-        best_d = d;
-        if (h == 0) break;
-      }
+      const uint32_t h = (x >= d) ? (uint32_t)__popcll((uint64_t)(c ^ cr[p - d])) : (uint32_t)k.nbits;
+      best = min(best, h << 9 | (uint32_t)d);
     }
   }
-  b.dhat[p] = (best_d >= 0 && best_h < k.ts) ? (int16_t)best_d : b.dbar[p];
+  b.dhat[p] = (best != 0xffffffffu && (int)(best >> 9) < k.ts) ? (int16_t)(best & 511u) : b.dbar[p];
 }
 
 cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStream_t s) {
@@ -563,9 +559,9 @@ cudaError_t launch_semidense(const KParams &k, const Buffers &b, int nf, cudaStr
 // choice: 256, 512 or 1024) and stages the right-census window of the
 // segment in shared memory once.  Then (1) one thread per pixel computes
 // d-hat of Eq. 5 from the box-ORed mask of its r_s window: the candidates are
-// the mask's set bits, each H taken from the staged window, visited in
-// increasing d so that the first strict minimum is the lexicographic (H, d)
-// minimum; d-hat = that d if min H < T_s, else d-bar (staging the
+// the mask's set bits, each H taken from the staged window; the smallest key
+// H << 9 | d over them is the lexicographic (H, d) minimum, with no branch
+// per candidate; d-hat = that d if min H < T_s, else d-bar (staging the
 // segment's mask words and d-bar with the census window instead was 13 %
 // slower: the whole CTA then waits on those loads); (2) a warp takes P = 4
 // consecutive pixels at a time,
@@ -631,23 +627,21 @@ __global__ void __launch_bounds__(256) k_cost_seg(KParams k, Buffers b0, const _
     if (SEMI) {
       const int x = x0 + i;
       const CT c = cl_s[i];
-      int best_h = 0x7fffffff, best_d = -1;
+      // the candidates in rising d; the smallest key H << 9 | d is the
+      // smallest H, ties to the smallest d (d < 512, H < 128)
+      uint32_t best = 0xffffffffu;
 #pragma unroll
       for (int w = 0; w < DPL; ++w) {
-        if (best_h == 0) break;
+        if (best < 512u) break;   // H = 0 found: no later candidate wins
         uint32_t m = mw_r[jj][w];
         while (m != 0u) {
           const int d = w * 32 + __ffs(m) - 1;
           m &= m - 1u;
-          const int h = x >= d ? hamming<CT>(c, cr_s[i + Dp - 1 - d]) : k.nbits;
-          if (h < best_h) {
-            best_h = h;
-            best_d = d;
-            if (h == 0) break;
-          }
+          const uint32_t h = x >= d ? (uint32_t)hamming<CT>(c, cr_s[i + Dp - 1 - d]) : (uint32_t)k.nbits;
+          best = min(best, h << 9 | (uint32_t)d);
         }
       }
-      pd = (best_d >= 0 && best_h < k.ts) ? best_d : db;
+      pd = (best != 0xffffffffu && (int)(best >> 9) < k.ts) ? (int)(best & 511u) : db;
       b.dhat[p] = (int16_t)pd;
     }
     pd_s[i] = (int16_t)pd;
